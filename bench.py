@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the confined-TTSH solver on GB300: grid-point-steps per second.
+
+One timed step = one segment of `--solver-steps` steps of Algorithm 1 on the workload's
+domain (default: the 512 x 512 circular domain, R = 5.4, dx = 0.04, uniform noise 0.01 from
+seed 2, 20000 solver steps).  The float32 path is the headline value; the float64 path is
+measured alongside under "fp64".  Multi-GPU (torchrun): every rank advances its own
+independent domain (seed + rank), no data-path collective; value = all ranks' grid-point-
+steps / the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the method written from the paper in numpy) on
+the same workload, on this machine's host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ttsh_inputs as ti  # noqa: E402
+
+METRIC = "grid-point-steps/s FP32 vs FP64 on 1 GB300; surrogate speedup at ≤2% error"
+UNIT = "grid-point-steps/s"
+DEFAULT_SOLVER_STEPS = {"circle512": 20000, "circle64_fp64": 2000, "circle2048_turbulent": 2000,
+                        "circle8192_paper_grid": 100}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="circle512", choices=sorted(ti.WORKLOADS))
+    ap.add_argument("--solver-steps", type=int, default=None)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(name, w, S):
+    return (f"{name}: one circular domain R={w['radius']} on a {w['n']}x{w['n']} periodic grid, "
+            f"dx={w['dx']}, Table I constants, dt=0.01, uniform noise 0.01 inside the mask "
+            f"(seed {w['seed']}), {S} solver steps per timed step")
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu_id)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        p = json.load(open(path))
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2304_03306_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, n, precision):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels."""
+    try:
+        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        e = t[f"{kernel}:{n}:{precision}"]
+        if e.get("csrc_hash") == csrc_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def algorithmic_bytes(n, elt):
+    """Bytes one launch of each pass must move (inputs read once, outputs written once)."""
+    H = n // 4 + 1
+    NK = n // 2 + 1
+    c = 2 * elt
+    row = 4 * H * n * c + n * n * elt + 3 * H * n * c
+    col = 3 * H * n * c + 2 * H * NK * c + 4 * H * n * c
+    return {"row_pass": row, "col_pass": col}
+
+
+# ----------------------------------------------------------------------- CPU oracle leg
+
+def time_oracle(w, budget_s=10.0, min_steps=3):
+    from oracle import ttsh_oracle as O
+    n, dx = w["n"], w["dx"]
+    mask = ti.circle_mask(n, dx, w["radius"])
+    vx, vy = ti.noise_velocity(mask, w["seed"], 0.01)
+    p = O.Params(n=n, dx=dx)
+    K = O.process_mask(mask)
+    s = O.project_velocity(vx, vy, p)
+    s = O.step(s, K, p)   # warm
+    steps, t0 = 0, time.perf_counter()
+    while steps < min_steps or time.perf_counter() - t0 < budget_s:
+        s = O.step(s, K, p)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return n * n * steps / dt, steps, dt
+
+
+# ------------------------------------------------------------------------ GPU leg
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2304_03306_gb300 import build, ttsh
+
+    build.build()
+    ttsh.load_library()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+
+    w = ti.WORKLOADS[args.workload]
+    n, dx = w["n"], w["dx"]
+    S = args.solver_steps or DEFAULT_SOLVER_STEPS.get(args.workload, 1000)
+    K, W = args.steps, args.warmup
+    mask = ti.circle_mask(n, dx, w["radius"])
+    vx0, vy0 = ti.noise_velocity(mask, w["seed"] + rank, 0.01)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    def timed_segments(dom, nseg, steps_per):
+        evs = []
+        for i in range(nseg):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dom.step(steps_per)
+            e1.record(stream)
+            evs.append((e0, e1))
+        stream.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / 1e3
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- float32 (headline) ----
+    dom = ttsh.Domain(mask, n, dx, precision=32, stream=stream.cuda_stream)
+    dom.set_velocity(vx0, vy0)
+    for _ in range(W):
+        dom.step(S)
+    dom.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    clocks = ClockSampler(vis[local_rank].strip() if local_rank < len(vis) else local_rank)
+    clocks.start()
+    t32 = timed_segments(dom, K, S)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    t32 = max_over_ranks(t32)
+    value = world * n * n * S * K / t32
+
+    # kernel-level timing for the roofline (same domain, same stream; state restored)
+    iters = max(50, min(2000, int(2e7 // (n * n))))
+    row_ms, col_ms = dom.time_kernels(iters)
+    diag = dom.diagnostics()
+    dom.close()
+
+    # ---- float64 alongside ----
+    fp64 = None
+    if not args.no_fp64:
+        d64 = ttsh.Domain(mask, n, dx, precision=64, stream=stream.cuda_stream)
+        d64.set_velocity(vx0, vy0)
+        S64 = max(1, S // 4)
+        d64.step(S64)
+        d64.synchronize()
+        barrier()
+        t64 = max_over_ranks(timed_segments(d64, K, S64))
+        r64, c64 = d64.time_kernels(max(20, iters // 4))
+        d64.close()
+        v64 = world * n * n * S64 * K / t64
+        fp64 = {"value": v64, "unit": UNIT, "solver_steps_per_step": S64,
+                "ms_per_solver_step": 1e3 * t64 / (S64 * K), "row_pass_ms": r64, "col_pass_ms": c64,
+                "fp32_over_fp64": value / v64}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda shape: torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy()
+        hx, hy = pin((n, n)), pin((n, n))
+        hx[:], hy[:] = vx0, vy0
+        ox, oy, ow = pin((n, n)), pin((n, n)), pin((n, n))
+        de = ttsh.Domain(mask, n, dx, precision=32, stream=stream.cuda_stream)
+        lib = ttsh.load_library()
+        P = lambda a: a.ctypes.data_as(ttsh._D)
+
+        def e2e_step():
+            ttsh._check(lib.ttsh_set_velocity(de.h, P(hx), P(hy)))
+            ttsh._check(lib.ttsh_step(de.h, S))
+            ttsh._check(lib.ttsh_get_fields(de.h, P(ox), P(oy), P(ow)))
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(K):
+            e2e_step()
+        te = max_over_ranks(time.perf_counter() - t0)
+        de.close()
+        e2e = {"value": world * n * n * S * K / te, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": 3 * n * n * 8}
+
+    if dist:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return None
+
+    # ---- roofline of the dominant kernel ----
+    elt = 4
+    ab = algorithmic_bytes(n, elt)
+    dom_k = "row_pass" if row_ms >= col_ms else "col_pass"
+    dom_ms = max(row_ms, col_ms)
+    peak, peak_src = peaks()
+    achieved = ab[dom_k] / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": ncu_traffic(dom_k, n, 32),
+                "kernel": dom_k, "kernel_ms": dom_ms, "algorithmic_bytes": ab[dom_k],
+                "peak_source": f"{peak_src} (copy bandwidth)",
+                "passes_ms": {"row_pass": row_ms, "col_pass": col_ms},
+                "share": {"row_pass": row_ms / (row_ms + col_ms), "col_pass": col_ms / (row_ms + col_ms)},
+                "step_bytes_per_point": (ab["row_pass"] + ab["col_pass"]) / (n * n)}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, steps, dt = time_oracle(w)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{steps} oracle (numpy FP64, single-threaded) steps of the same {n}x{n} workload in {dt:.1f} s"}
+
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * t32 / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_desc(args.workload, w, S), "n": n, "dx": dx,
+                   "radius": w["radius"], "solver_steps_per_step": S,
+                   "l2": "flushed (256 MiB write) before every timed step; the state stays L2-resident within a step",
+                   "parallelism": "replicas" if world == 1 else f"independent domains x{world}"},
+        "e2e": e2e, "gpu_launches": 2 * S * K, "clocks": clk, "roofline": roofline,
+        "cpu_baseline": cpu, "fp64": fp64,
+        "diagnostics_after": {"energy": diag["energy"], "psi": diag["psi"], "nonfinite": diag["nonfinite"]},
+        "ms_per_solver_step": 1e3 * t32 / (K * S),
+    }
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w = ti.WORKLOADS[args.workload]
+    n = w["n"]
+    from oracle import ttsh_oracle as O
+    mask = ti.circle_mask(n, w["dx"], w["radius"])
+    vx, vy = ti.noise_velocity(mask, w["seed"], 0.01)
+    p = O.Params(n=n, dx=w["dx"])
+    K_ = O.process_mask(mask)
+    s = O.project_velocity(vx, vy, p)
+    S_ref = max(1, int(2.0e6 // (n * n)))   # ~1 s of oracle work per step at 512^2
+    for _ in range(args.warmup):
+        s = O.run(s, K_, p, S_ref)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s = O.run(s, K_, p, S_ref)
+    dt = time.perf_counter() - t0
+    v = n * n * S_ref * args.steps / dt
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload, w, S_ref), "n": n,
+                       "solver_steps_per_step": S_ref, "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{S_ref * args.steps} oracle steps of the {n}x{n} workload"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local_rank)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * ttsh.h - C ABI of the GB300 (sm_103a) solver for the confined Toner-Tu-Swift-Hohenberg
+ * (TTSH) polar-active-fluid model of arXiv:2304.03306.
+ *
+ * The model is the vorticity form of the TTSH equation with damping mask K(x), Eq. (mod1)-
+ * (mod2) (Sec. II.A), with the constants of Table I.  A domain is one N x N periodic box
+ * (L = N dx) whose boundary is given only as a binary mask K_naive (Sec. II.C); the library
+ * turns it into the band-limited, non-negative K of Algorithm 2 (Appendix E) and time-steps
+ * the state with the pseudospectral integrating-factor Euler scheme of Algorithm 1
+ * (Appendix D).  All arithmetic of a step runs in this library's CUDA kernels.
+ *
+ * Conventions shared by every entry point:
+ *  - Real fields are N*N arrays indexed [y][x] (row-major), grid point (i, j) at
+ *    x = (j - N/2) dx, y = (i - N/2) dx.
+ *  - The DFT is the unitary one of Appendix D: f^(k) = N^-1 sum_x f(x) e^{-i k.x}, inverse
+ *    with e^{+i k.x} and N^-1; k = dk * m, dk = 2 pi / (N dx), m integer.
+ *  - The spectral state omega^ is stored as the Hermitian half-spectrum restricted to the
+ *    1/2-rule disc: columns mx = 0..N/4 ("H = N/4 + 1" columns), each holding
+ *    "NK = N/2 + 1" values for my = 0..N/4 then my = -N/4..-1 (entry j <-> my = j for
+ *    j <= N/4, my = j - NK otherwise).  Modes with mx^2 + my^2 > (N/4)^2 are zero.  The
+ *    spatial mean velocity v^(0) (two reals, unitary DFT at k = 0, i.e. N * mean) is kept
+ *    separately, as Algorithm 1 does at k = 0.
+ *  - Host pointers are owned by the caller and are only read/written during the call.
+ *  - Every call returns a ttsh_status; no C++ exception crosses the ABI.  A thread-local
+ *    message for the last failure is returned by ttsh_last_error().
+ *  - Kernels run on the domain's stream.  ttsh_step is asynchronous; calls that return
+ *    host data synchronise the stream first.  A device-side failure surfaces as
+ *    TTSH_E_CUDA at the next synchronising call.
+ */
+#ifndef TTSH_H
+#define TTSH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TTSH_OK = 0,
+  TTSH_E_INVALID = 1,      /* bad argument (size, pointer, parameter value)              */
+  TTSH_E_OOM = 2,          /* device allocation failed                                    */
+  TTSH_E_CUDA = 3,         /* a CUDA runtime call or kernel failed                        */
+  TTSH_E_TIMEOUT = 4,      /* reserved: a bounded device wait ran out                     */
+  TTSH_E_NONFINITE = 5,    /* the state holds NaN or Inf (reported by ttsh_diagnostics)   */
+  TTSH_E_UNSUPPORTED = 6   /* a valid request this build does not implement              */
+} ttsh_status;
+
+/* Model and discretisation constants.  Defaults (ttsh_default_params) are Table I:
+ * a = 0.5, b = 1.6, lambda = 9, gamma_v = 40, gamma_w = 4, dt = 0.01, N = 8192, dx = 0.005.
+ * n must be a power of two in [16, 8192]; precision is 32 (float) or 64 (double) and
+ * selects the arithmetic of every kernel of the domain. */
+typedef struct {
+  double a, b, lambda, gamma_v, gamma_w;
+  double dx, dt;
+  int32_t n;
+  int32_t precision;
+} ttsh_params;
+
+/* Observables of the current state, accumulated in double precision whatever the
+ * domain precision (sums in a fixed order, so repeated calls give identical bits):
+ *   energy    = (2 N^2)^-1 sum_x |v|^2
+ *   enstrophy = (2 N^2)^-1 sum_x omega^2
+ *   psi       = vortex order parameter of Sec. III.C: (sum|e_theta.v| / sum|v| - 2/pi)
+ *               / (1 - 2/pi) over every grid point, about the given centre (e_theta := 0
+ *               at the centre itself)
+ *   mean_vx, mean_vy = spatial mean of v (= v^(0) / N)
+ *   nonfinite = number of non-finite values met in the state's real-space fields. */
+typedef struct {
+  double energy, enstrophy, psi, mean_vx, mean_vy;
+  int64_t step;
+  int32_t nonfinite;
+  int32_t reserved;
+} ttsh_diag;
+
+typedef struct ttsh_domain ttsh_domain;
+
+/* Fill *p with the Table I constants (Appendix B).  Never fails. */
+void ttsh_default_params(ttsh_params* p);
+
+/* Bytes of device memory one domain with these parameters uses (state, mask, the two
+ * inter-pass buffers, staging and reduction scratch, twiddle table), or 0 if the
+ * parameters are invalid.  Passing a caller-owned block of at least this size (256-byte
+ * aligned) to ttsh_create_domain makes the library allocate nothing. */
+size_t ttsh_workspace_bytes(const ttsh_params* p);
+
+/* Create a domain from a binary mask (Sec. II.C; Algorithm 2 of Appendix E runs on the
+ * GPU: DFT, zero |m|^2 > (N/8)^2, inverse DFT, square).
+ *   mask       host, N*N bytes [y][x]; nonzero = masked (K_naive = 1), 0 = inside.
+ *   p          parameters; validated (n power of two in [16, 8192], dx > 0, dt > 0,
+ *              precision 32 or 64) -> TTSH_E_INVALID otherwise.
+ *   workspace  device pointer of ttsh_workspace_bytes(p) bytes owned by the caller (it
+ *              must outlive the domain), or NULL to let the library cudaMalloc it.
+ *   stream     cudaStream_t the domain's kernels are issued on (NULL = legacy default).
+ *   out        receives the handle.
+ * The state starts at zero (omega^ = 0, v^(0) = 0). */
+ttsh_status ttsh_create_domain(const uint8_t* mask, const ttsh_params* p, void* workspace,
+                               void* stream, ttsh_domain** out);
+
+/* Release the domain (and its workspace if the library allocated it).  NULL is a no-op. */
+void ttsh_destroy_domain(ttsh_domain* d);
+
+/* Change the stream later kernels are issued on. */
+ttsh_status ttsh_set_stream(ttsh_domain* d, void* stream);
+
+/* Set the state from a real velocity field (host, N*N doubles each).  The field is
+ * projected as the initial condition of the method: omega^ = i k x v^, then Algorithm 1's
+ * post-processing (omega^(0) = 0, v^(0) = DFT[v](0), zero |m|^2 > (N/4)^2, Hermitian
+ * average, v from the stream function), so the stored state is divergence-free and
+ * band-limited.  Resets the step counter. */
+ttsh_status ttsh_set_velocity(ttsh_domain* d, const double* vx, const double* vy);
+
+/* Same, from a real velocity field already on the device (N*N doubles each, any
+ * 8-byte-aligned device pointers, read during the call only). */
+ttsh_status ttsh_set_velocity_device(ttsh_domain* d, const double* vx, const double* vy);
+
+/* Advance the state by nsteps steps of Algorithm 1 (Appendix D): real-space nonlinear and
+ * mask terms (lines 1-2), DFT of the right-hand side and curl assembly (line 3), the
+ * integrating-factor Euler update (line 4), the k = 0 mean-flow update of Eq. (avg)
+ * (lines 6-8), the 1/2-rule dealiasing (lines 9-11), the Hermitian average and the
+ * stream-function velocity (lines 13-15).  Asynchronous on the domain's stream; long runs
+ * are replayed as CUDA graphs.  nsteps < 0 -> TTSH_E_INVALID; 0 is a no-op. */
+ttsh_status ttsh_step(ttsh_domain* d, int64_t nsteps);
+
+/* Copy the real-space fields of the current state to the host (N*N doubles each, [y][x]):
+ * v_x, v_y (including the mean flow) and omega = iDFT[omega^].  Any pointer may be NULL. */
+ttsh_status ttsh_get_fields(ttsh_domain* d, double* vx, double* vy, double* omega);
+
+/* Copy the processed mask K of Algorithm 2 (N*N doubles, [y][x]) to the host. */
+ttsh_status ttsh_get_mask(ttsh_domain* d, double* K);
+
+/* Checkpoint / resume of the exact state: omega^ as interleaved (re, im) doubles in the
+ * half-spectrum layout described above (H * NK complex values, column mx-major), and
+ * v^(0) as 2 doubles.  set_spectral_state converts to the domain precision (exact for a
+ * state read back from a domain of the same precision, so a resumed run is bit-identical)
+ * and does not alter the values (no re-projection). */
+ttsh_status ttsh_get_spectral_state(ttsh_domain* d, double* w_hat, double* v0);
+ttsh_status ttsh_set_spectral_state(ttsh_domain* d, const double* w_hat, const double* v0);
+
+/* Diagnostics of the current state (see ttsh_diag).  centre: (x, y) of the centre used by
+ * psi, NULL = (0, 0).  spectrum: if non-NULL, receives nbins doubles of the shell energy
+ * spectrum E(s) = (2 N^2)^-1 sum over modes with round(|m|) = s of |v^(m)|^2; shells beyond
+ * N/4 are zero.  nbins must be in [0, 65536].  Synchronises.  Returns TTSH_E_NONFINITE
+ * (with *out filled) when the state holds NaN/Inf. */
+ttsh_status ttsh_diagnostics(ttsh_domain* d, ttsh_diag* out, double* spectrum, int32_t nbins,
+                             const double* centre);
+
+/* Kernel timing for roofline reports: launches the row pass `iters` times back to back and
+ * then the column pass `iters` times, each run bracketed by CUDA events on the domain's
+ * stream, and writes the mean duration of one launch in milliseconds to ms[0] (row pass)
+ * and ms[1] (column pass).  The spectral state and inter-pass buffers are saved before and
+ * restored after, so the domain continues exactly where it was.  Synchronises.
+ * iters must be in [1, 1000000]. */
+ttsh_status ttsh_time_kernels(ttsh_domain* d, int32_t iters, double* ms);
+
+/* Block the host until the domain's stream is idle; reports deferred CUDA errors. */
+ttsh_status ttsh_synchronize(ttsh_domain* d);
+
+/* Steps taken since the last set_velocity / set_spectral_state. */
+int64_t ttsh_step_count(const ttsh_domain* d);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* ttsh_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TTSH_H */

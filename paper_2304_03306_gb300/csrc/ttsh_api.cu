@@ -1,0 +1,575 @@
+// ttsh_api.cu - host runtime behind the C ABI of include/ttsh.h.
+//
+// A domain owns (or borrows) one device workspace holding the spectral state, the processed
+// mask, the two inter-pass buffers of the row/column step, a double staging area for host
+// transfers, the diagnostics scratch and the twiddle table.  Every arithmetic step of the
+// method runs in the kernels of ttsh_kernels.cuh; this file only validates arguments,
+// carves the workspace, orders launches on the domain's stream and records multi-step
+// loops as CUDA graphs.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ttsh.h"
+#include "ttsh_kernels.cuh"
+#include "ttsh_ops.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ttsh_status fail(ttsh_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+ttsh_status cuda_fail(cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(e == cudaErrorMemoryAllocation ? TTSH_E_OOM : TTSH_E_CUDA, m);
+}
+
+#define TTSH_CUDA(call, what)                      \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+struct Layout {
+  size_t what, vmean, K, G, Rr, tw, real, part, colhist, bad, out, save, total;
+};
+
+Layout layout_for(int n, size_t elt) {
+  const size_t M = n / 4, H = M + 1, NK = 2 * M + 1, NN = (size_t)n * n;
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align_up(bytes);
+    return o;
+  };
+  L.what = take(H * NK * 2 * elt);
+  L.vmean = take(64);
+  L.K = take(NN * elt);
+  L.G = take(4 * H * n * 2 * elt);
+  L.Rr = take(3 * H * n * 2 * elt);
+  L.tw = take((size_t)n * 2 * elt);
+  L.real = take(3 * NN * sizeof(double));
+  L.part = take((size_t)n * ttsh::kDiagQ * sizeof(double));
+  L.colhist = take(H * (M + 1) * sizeof(double));
+  L.bad = take(64);
+  L.out = take((8 + M + 1) * sizeof(double));
+  L.save = take(H * NK * 2 * elt + 64);   // state copy kept by ttsh_time_kernels
+  L.total = off;
+  return L;
+}
+
+ttsh_status validate(const ttsh_params* p) {
+  if (!p) return fail(TTSH_E_INVALID, "params is NULL");
+  if (!is_pow2(p->n) || p->n < 16 || p->n > 8192)
+    return fail(TTSH_E_INVALID, "n must be a power of two in [16, 8192]");
+  if (p->precision != 32 && p->precision != 64)
+    return fail(TTSH_E_INVALID, "precision must be 32 or 64");
+  if (!(p->dx > 0) || !(p->dt > 0) || !std::isfinite(p->dx) || !std::isfinite(p->dt))
+    return fail(TTSH_E_INVALID, "dx and dt must be positive and finite");
+  const double c[5] = {p->a, p->b, p->lambda, p->gamma_v, p->gamma_w};
+  for (double v : c)
+    if (!std::isfinite(v)) return fail(TTSH_E_INVALID, "model coefficients must be finite");
+  return TTSH_OK;
+}
+
+bool find_ops(int n, int precision, ttsh::SizeOps* o) {
+  if (precision == 32) return ttsh::ops_f32_small(n, o) || ttsh::ops_f32_large(n, o);
+  return ttsh::ops_f64_small(n, o) || ttsh::ops_f64_large(n, o);
+}
+
+// Twiddles W_N^m = exp(-2 pi i m / N), computed in extended precision and rounded once.
+template <typename T>
+std::vector<T> twiddles(int n) {
+  std::vector<T> tw(2 * (size_t)n);
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int m = 0; m < n; ++m) {
+    const long double ang = two_pi * (long double)m / (long double)n;
+    tw[2 * m] = (T)(double)cosl(ang);
+    tw[2 * m + 1] = (T)(double)(-sinl(ang));
+  }
+  return tw;
+}
+
+}  // namespace
+
+struct ttsh_domain {
+  ttsh_params p;
+  int n, M, H, NK;
+  size_t elt;
+  cudaStream_t stream;
+  cudaStream_t capture;     // private stream used only to record graphs
+  void* ws;
+  bool owns_ws;
+  Layout lay;
+  ttsh::DomainDev dev;
+  ttsh::SizeOps ops;
+  int64_t steps;
+  cudaGraphExec_t graph;
+  int graph_len;
+};
+
+namespace {
+
+constexpr int kGraphLen = 64;   // steps recorded per graph replay
+
+ttsh_status run_row(ttsh_domain* d, int kind, cudaStream_t s) {
+  cudaError_t e = d->ops.row(kind, d->dev, s);
+  if (e != cudaSuccess) return cuda_fail(e, "row kernel launch");
+  return TTSH_OK;
+}
+
+ttsh_status run_col(ttsh_domain* d, int mode, cudaStream_t s) {
+  cudaError_t e = d->ops.col(mode, d->dev, s);
+  if (e != cudaSuccess) return cuda_fail(e, "column kernel launch");
+  return TTSH_OK;
+}
+
+ttsh_status one_step(ttsh_domain* d, cudaStream_t s) {
+  ttsh_status st = run_row(d, ttsh::K_ROW_STEP, s);
+  if (st != TTSH_OK) return st;
+  return run_col(d, ttsh::K_COL_STEP, s);
+}
+
+ttsh_status sync(ttsh_domain* d, const char* what) {
+  TTSH_CUDA(cudaStreamSynchronize(d->stream), what);
+  return TTSH_OK;
+}
+
+ttsh_status build_graph(ttsh_domain* d) {
+  // The capture runs on a private stream; replays are launched on the domain's stream.
+  TTSH_CUDA(cudaStreamBeginCapture(d->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+  ttsh_status st = TTSH_OK;
+  for (int i = 0; i < kGraphLen && st == TTSH_OK; ++i) st = one_step(d, d->capture);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(d->capture, &g);
+  if (st != TTSH_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "end capture");
+  e = cudaGraphInstantiate(&d->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    d->graph = nullptr;
+    return cuda_fail(e, "graph instantiate");
+  }
+  d->graph_len = kGraphLen;
+  return TTSH_OK;
+}
+
+ttsh_status project_staged(ttsh_domain* d) {
+  ttsh_status st = run_row(d, ttsh::K_ROW_FWD_VEL, d->stream);
+  if (st != TTSH_OK) return st;
+  st = run_col(d, ttsh::K_COL_PROJECT, d->stream);
+  if (st != TTSH_OK) return st;
+  d->steps = 0;
+  return sync(d, "set_velocity");
+}
+
+template <typename T>
+void to_host_double(const std::vector<T>& src, double* dst) {
+  for (size_t i = 0; i < src.size(); ++i) dst[i] = (double)src[i];
+}
+
+}  // namespace
+
+namespace ttsh {
+
+__global__ void diag_reduce_kernel(const double* __restrict__ part, int nblocks, double* out) {
+  __shared__ double red[kDiagQ][256];
+  const int t = threadIdx.x;
+  double acc[kDiagQ] = {0, 0, 0, 0, 0};
+  for (int i = t; i < nblocks; i += 256)
+    for (int q = 0; q < kDiagQ; ++q) acc[q] += part[(size_t)i * kDiagQ + q];
+  for (int q = 0; q < kDiagQ; ++q) red[q][t] = acc[q];
+  __syncthreads();
+  for (int s = 128; s >= 1; s >>= 1) {
+    if (t < s)
+      for (int q = 0; q < kDiagQ; ++q) red[q][t] += red[q][t + s];
+    __syncthreads();
+  }
+  if (t < kDiagQ) out[t] = red[t][0];
+}
+
+__global__ void spectrum_reduce_kernel(const double* __restrict__ colhist, int ncols, int nbins,
+                                       double scale, double* __restrict__ out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nbins) return;
+  double acc = 0.0;
+  for (int c = 0; c < ncols; ++c) acc += colhist[(size_t)c * nbins + s];
+  out[s] = acc * scale;
+}
+
+cudaError_t launch_diag_reduce(const double* part, int nblocks, double* out, cudaStream_t s) {
+  diag_reduce_kernel<<<1, 256, 0, s>>>(part, nblocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum_reduce(const double* colhist, int ncols, int nbins, double scale,
+                                   double* out, cudaStream_t s) {
+  spectrum_reduce_kernel<<<(nbins + 127) / 128, 128, 0, s>>>(colhist, ncols, nbins, scale, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ttsh
+
+extern "C" {
+
+void ttsh_default_params(ttsh_params* p) {
+  if (!p) return;
+  p->a = 0.5;
+  p->b = 1.6;
+  p->lambda = 9.0;
+  p->gamma_v = 40.0;
+  p->gamma_w = 4.0;
+  p->dx = 0.005;
+  p->dt = 0.01;
+  p->n = 8192;
+  p->precision = 32;
+}
+
+size_t ttsh_workspace_bytes(const ttsh_params* p) {
+  if (validate(p) != TTSH_OK) return 0;
+  return layout_for(p->n, p->precision == 32 ? sizeof(float) : sizeof(double)).total;
+}
+
+ttsh_status ttsh_create_domain(const uint8_t* mask, const ttsh_params* p, void* workspace,
+                               void* stream, ttsh_domain** out) {
+  g_last_error.clear();
+  if (!out) return fail(TTSH_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!mask) return fail(TTSH_E_INVALID, "mask is NULL");
+  ttsh_status st = validate(p);
+  if (st != TTSH_OK) return st;
+  if (workspace && (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0)
+    return fail(TTSH_E_INVALID, "workspace must be 256-byte aligned");
+  ttsh::SizeOps ops;
+  if (!find_ops(p->n, p->precision, &ops))
+    return fail(TTSH_E_UNSUPPORTED, "no kernels for this (n, precision): double precision supports n <= 4096");
+
+  ttsh_domain* d = new ttsh_domain();
+  d->p = *p;
+  d->n = p->n;
+  d->M = p->n / 4;
+  d->H = d->M + 1;
+  d->NK = 2 * d->M + 1;
+  d->elt = p->precision == 32 ? sizeof(float) : sizeof(double);
+  d->stream = static_cast<cudaStream_t>(stream);
+  d->capture = nullptr;
+  d->ops = ops;
+  d->steps = 0;
+  d->graph = nullptr;
+  d->graph_len = 0;
+  d->lay = layout_for(d->n, d->elt);
+  d->owns_ws = workspace == nullptr;
+  d->ws = workspace;
+  auto cleanup = [&](ttsh_status s) {
+    ttsh_destroy_domain(d);
+    return s;
+  };
+  if (d->owns_ws) {
+    cudaError_t e = cudaMalloc(&d->ws, d->lay.total);
+    if (e != cudaSuccess) {
+      d->ws = nullptr;
+      return cleanup(cuda_fail(e, "workspace allocation"));
+    }
+  }
+  {
+    cudaError_t e = cudaStreamCreateWithFlags(&d->capture, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "capture stream"));
+  }
+  char* base = static_cast<char*>(d->ws);
+  ttsh::DomainDev& v = d->dev;
+  v.what = base + d->lay.what;
+  v.vmean = base + d->lay.vmean;
+  v.K = base + d->lay.K;
+  v.G = base + d->lay.G;
+  v.Rr = base + d->lay.Rr;
+  v.tw = base + d->lay.tw;
+  v.real = reinterpret_cast<double*>(base + d->lay.real);
+  v.part = reinterpret_cast<double*>(base + d->lay.part);
+  v.colhist = reinterpret_cast<double*>(base + d->lay.colhist);
+  v.bad = reinterpret_cast<int*>(base + d->lay.bad);
+  v.out = reinterpret_cast<double*>(base + d->lay.out);
+  v.a = p->a;
+  v.b = p->b;
+  v.lam = p->lambda;
+  v.gv = p->gamma_v;
+  v.gw = p->gamma_w;
+  v.dx = p->dx;
+  v.dt = p->dt;
+  v.cx = 0.0;
+  v.cy = 0.0;
+  v.n = p->n;
+
+  const size_t NN = (size_t)d->n * d->n;
+  cudaStream_t s = d->stream;
+  // twiddle table
+  if (d->elt == sizeof(float)) {
+    std::vector<float> tw = twiddles<float>(d->n);
+    cudaError_t e = cudaMemcpyAsync(v.tw, tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "twiddle upload"));
+  } else {
+    std::vector<double> tw = twiddles<double>(d->n);
+    cudaError_t e = cudaMemcpyAsync(v.tw, tw.data(), tw.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "twiddle upload"));
+  }
+  // Algorithm 2 on the device: K_naive (0/1) -> DFT -> |m|^2 <= (N/8)^2 -> iDFT -> square.
+  {
+    std::vector<double> kn(NN);
+    for (size_t i = 0; i < NN; ++i) kn[i] = mask[i] ? 1.0 : 0.0;
+    cudaError_t e = cudaMemcpyAsync(v.real, kn.data(), NN * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "mask upload"));
+  }
+  if ((st = run_row(d, ttsh::K_ROW_FWD_MASK, s)) != TTSH_OK) return cleanup(st);
+  if ((st = run_col(d, ttsh::K_COL_MASK, s)) != TTSH_OK) return cleanup(st);
+  if ((st = run_row(d, ttsh::K_ROW_INV_MASK, s)) != TTSH_OK) return cleanup(st);
+  // zero state, consistent inter-pass buffers
+  {
+    cudaError_t e = cudaMemsetAsync(v.what, 0, (size_t)d->H * d->NK * 2 * d->elt, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v.vmean, 0, 64, s);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "state init"));
+  }
+  if ((st = run_col(d, ttsh::K_COL_PROLOGUE, s)) != TTSH_OK) return cleanup(st);
+  if ((st = sync(d, "create_domain")) != TTSH_OK) return cleanup(st);
+  *out = d;
+  return TTSH_OK;
+}
+
+void ttsh_destroy_domain(ttsh_domain* d) {
+  if (!d) return;
+  if (d->graph) cudaGraphExecDestroy(d->graph);
+  if (d->capture) cudaStreamDestroy(d->capture);
+  if (d->owns_ws && d->ws) cudaFree(d->ws);
+  delete d;
+}
+
+ttsh_status ttsh_set_stream(ttsh_domain* d, void* stream) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  d->stream = static_cast<cudaStream_t>(stream);
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_set_velocity(ttsh_domain* d, const double* vx, const double* vy) {
+  if (!d || !vx || !vy) return fail(TTSH_E_INVALID, "NULL argument");
+  const size_t NN = (size_t)d->n * d->n;
+  TTSH_CUDA(cudaMemcpyAsync(d->dev.real, vx, NN * sizeof(double), cudaMemcpyHostToDevice, d->stream), "upload vx");
+  TTSH_CUDA(cudaMemcpyAsync(d->dev.real + NN, vy, NN * sizeof(double), cudaMemcpyHostToDevice, d->stream), "upload vy");
+  return project_staged(d);
+}
+
+ttsh_status ttsh_set_velocity_device(ttsh_domain* d, const double* vx, const double* vy) {
+  if (!d || !vx || !vy) return fail(TTSH_E_INVALID, "NULL argument");
+  const size_t NN = (size_t)d->n * d->n;
+  TTSH_CUDA(cudaMemcpyAsync(d->dev.real, vx, NN * sizeof(double), cudaMemcpyDeviceToDevice, d->stream), "copy vx");
+  TTSH_CUDA(cudaMemcpyAsync(d->dev.real + NN, vy, NN * sizeof(double), cudaMemcpyDeviceToDevice, d->stream), "copy vy");
+  return project_staged(d);
+}
+
+ttsh_status ttsh_step(ttsh_domain* d, int64_t nsteps) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  if (nsteps < 0) return fail(TTSH_E_INVALID, "nsteps must be >= 0");
+  ttsh_status st;
+  int64_t left = nsteps;
+  if (left >= 2 * kGraphLen && !d->graph) {
+    // one eager step first: it sets the kernels' shared-memory attributes outside capture
+    if ((st = one_step(d, d->stream)) != TTSH_OK) return st;
+    --left;
+    d->steps += 1;
+    if ((st = build_graph(d)) != TTSH_OK) return st;
+  }
+  if (d->graph) {
+    while (left >= d->graph_len) {
+      TTSH_CUDA(cudaGraphLaunch(d->graph, d->stream), "graph launch");
+      left -= d->graph_len;
+      d->steps += d->graph_len;
+    }
+  }
+  for (; left > 0; --left) {
+    if ((st = one_step(d, d->stream)) != TTSH_OK) return st;
+    d->steps += 1;
+  }
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_get_fields(ttsh_domain* d, double* vx, double* vy, double* omega) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  ttsh_status st = run_row(d, ttsh::K_ROW_INV_FIELDS, d->stream);
+  if (st != TTSH_OK) return st;
+  const size_t NN = (size_t)d->n * d->n;
+  double* dst[3] = {omega, vx, vy};
+  for (int f = 0; f < 3; ++f)
+    if (dst[f])
+      TTSH_CUDA(cudaMemcpyAsync(dst[f], d->dev.real + f * NN, NN * sizeof(double), cudaMemcpyDeviceToHost, d->stream),
+                "download fields");
+  return sync(d, "get_fields");
+}
+
+ttsh_status ttsh_get_mask(ttsh_domain* d, double* K) {
+  if (!d || !K) return fail(TTSH_E_INVALID, "NULL argument");
+  const size_t NN = (size_t)d->n * d->n;
+  if (d->elt == sizeof(float)) {
+    std::vector<float> h(NN);
+    TTSH_CUDA(cudaMemcpyAsync(h.data(), d->dev.K, NN * sizeof(float), cudaMemcpyDeviceToHost, d->stream), "download K");
+    if ((sync(d, "get_mask")) != TTSH_OK) return TTSH_E_CUDA;
+    to_host_double(h, K);
+  } else {
+    TTSH_CUDA(cudaMemcpyAsync(K, d->dev.K, NN * sizeof(double), cudaMemcpyDeviceToHost, d->stream), "download K");
+    return sync(d, "get_mask");
+  }
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_get_spectral_state(ttsh_domain* d, double* w_hat, double* v0) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  const size_t ne = (size_t)d->H * d->NK * 2;
+  if (d->elt == sizeof(float)) {
+    std::vector<float> h(ne), m(2);
+    if (w_hat) TTSH_CUDA(cudaMemcpyAsync(h.data(), d->dev.what, ne * sizeof(float), cudaMemcpyDeviceToHost, d->stream), "download state");
+    TTSH_CUDA(cudaMemcpyAsync(m.data(), d->dev.vmean, 2 * sizeof(float), cudaMemcpyDeviceToHost, d->stream), "download mean");
+    ttsh_status st = sync(d, "get_spectral_state");
+    if (st != TTSH_OK) return st;
+    if (w_hat) to_host_double(h, w_hat);
+    if (v0) to_host_double(m, v0);
+  } else {
+    if (w_hat) TTSH_CUDA(cudaMemcpyAsync(w_hat, d->dev.what, ne * sizeof(double), cudaMemcpyDeviceToHost, d->stream), "download state");
+    double m[2];
+    TTSH_CUDA(cudaMemcpyAsync(m, d->dev.vmean, 2 * sizeof(double), cudaMemcpyDeviceToHost, d->stream), "download mean");
+    ttsh_status st = sync(d, "get_spectral_state");
+    if (st != TTSH_OK) return st;
+    if (v0) {
+      v0[0] = m[0];
+      v0[1] = m[1];
+    }
+  }
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_set_spectral_state(ttsh_domain* d, const double* w_hat, const double* v0) {
+  if (!d || !w_hat || !v0) return fail(TTSH_E_INVALID, "NULL argument");
+  const size_t ne = (size_t)d->H * d->NK * 2;
+  ttsh_status st;
+  if (d->elt == sizeof(float)) {
+    std::vector<float> h(ne), m(2);
+    for (size_t i = 0; i < ne; ++i) h[i] = (float)w_hat[i];
+    m[0] = (float)v0[0];
+    m[1] = (float)v0[1];
+    TTSH_CUDA(cudaMemcpyAsync(d->dev.what, h.data(), ne * sizeof(float), cudaMemcpyHostToDevice, d->stream), "upload state");
+    TTSH_CUDA(cudaMemcpyAsync(d->dev.vmean, m.data(), 2 * sizeof(float), cudaMemcpyHostToDevice, d->stream), "upload mean");
+    if ((st = sync(d, "set_spectral_state")) != TTSH_OK) return st;   // host vectors die here
+  } else {
+    TTSH_CUDA(cudaMemcpyAsync(d->dev.what, w_hat, ne * sizeof(double), cudaMemcpyHostToDevice, d->stream), "upload state");
+    TTSH_CUDA(cudaMemcpyAsync(d->dev.vmean, v0, 2 * sizeof(double), cudaMemcpyHostToDevice, d->stream), "upload mean");
+  }
+  if ((st = run_col(d, ttsh::K_COL_PROLOGUE, d->stream)) != TTSH_OK) return st;
+  d->steps = 0;
+  return sync(d, "set_spectral_state");
+}
+
+ttsh_status ttsh_diagnostics(ttsh_domain* d, ttsh_diag* out, double* spectrum, int32_t nbins,
+                             const double* centre) {
+  if (!d || !out) return fail(TTSH_E_INVALID, "NULL argument");
+  if (nbins < 0 || nbins > 65536) return fail(TTSH_E_INVALID, "nbins must be in [0, 65536]");
+  if (nbins > 0 && !spectrum) return fail(TTSH_E_INVALID, "spectrum is NULL");
+  d->dev.cx = centre ? centre[0] : 0.0;
+  d->dev.cy = centre ? centre[1] : 0.0;
+  const int nb_dev = d->M + 1;   // shells beyond N/4 hold no energy
+  cudaStream_t s = d->stream;
+  ttsh_status st = run_row(d, ttsh::K_ROW_INV_DIAG, s);
+  if (st != TTSH_OK) return st;
+  const int nblocks = d->ops.row_blocks(ttsh::K_ROW_INV_DIAG);
+  TTSH_CUDA(ttsh::launch_diag_reduce(d->dev.part, nblocks, d->dev.out, s), "diag reduce");
+  TTSH_CUDA(cudaMemsetAsync(d->dev.bad, 0, sizeof(int), s), "memset");
+  TTSH_CUDA(d->ops.spec(d->dev, nb_dev, s), "spectrum kernel");
+  const double scale = 1.0 / (2.0 * (double)d->n * (double)d->n);
+  TTSH_CUDA(ttsh::launch_spectrum_reduce(d->dev.colhist, d->H, nb_dev, scale, d->dev.out + 8, s), "spectrum reduce");
+  std::vector<double> h(8 + nb_dev);
+  int bad = 0;
+  TTSH_CUDA(cudaMemcpyAsync(h.data(), d->dev.out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "download diag");
+  TTSH_CUDA(cudaMemcpyAsync(&bad, d->dev.bad, sizeof(int), cudaMemcpyDeviceToHost, s), "download flag");
+  double vm[2];
+  if (d->elt == sizeof(float)) {
+    float f[2];
+    TTSH_CUDA(cudaMemcpyAsync(f, d->dev.vmean, sizeof(f), cudaMemcpyDeviceToHost, s), "download mean");
+    if ((st = sync(d, "diagnostics")) != TTSH_OK) return st;
+    vm[0] = f[0];
+    vm[1] = f[1];
+  } else {
+    TTSH_CUDA(cudaMemcpyAsync(vm, d->dev.vmean, sizeof(vm), cudaMemcpyDeviceToHost, s), "download mean");
+    if ((st = sync(d, "diagnostics")) != TTSH_OK) return st;
+  }
+  const double inv2n2 = 1.0 / (2.0 * (double)d->n * (double)d->n);
+  const double two_over_pi = 0.63661977236758134307553505349005744813783858296183;
+  out->energy = h[0] * inv2n2;
+  out->enstrophy = h[1] * inv2n2;
+  out->psi = (h[2] / h[3] - two_over_pi) / (1.0 - two_over_pi);
+  out->mean_vx = vm[0] / d->n;
+  out->mean_vy = vm[1] / d->n;
+  out->step = d->steps;
+  out->nonfinite = (int32_t)h[4] + bad;
+  out->reserved = 0;
+  for (int i = 0; i < nbins; ++i) spectrum[i] = i < nb_dev ? h[8 + i] : 0.0;
+  if (out->nonfinite) return fail(TTSH_E_NONFINITE, "state holds non-finite values");
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_time_kernels(ttsh_domain* d, int32_t iters, double* ms) {
+  if (!d || !ms) return fail(TTSH_E_INVALID, "NULL argument");
+  if (iters < 1 || iters > 1000000) return fail(TTSH_E_INVALID, "iters must be in [1, 1000000]");
+  cudaStream_t s = d->stream;
+  const size_t wbytes = (size_t)d->H * d->NK * 2 * d->elt;
+  char* save = static_cast<char*>(d->ws) + d->lay.save;
+  TTSH_CUDA(cudaMemcpyAsync(save, d->dev.what, wbytes, cudaMemcpyDeviceToDevice, s), "save state");
+  TTSH_CUDA(cudaMemcpyAsync(save + wbytes, d->dev.vmean, 64, cudaMemcpyDeviceToDevice, s), "save mean");
+  cudaEvent_t ev[4];
+  for (int i = 0; i < 4; ++i) TTSH_CUDA(cudaEventCreate(&ev[i]), "event create");
+  ttsh_status st = TTSH_OK;
+  cudaEventRecord(ev[0], s);
+  for (int i = 0; i < iters && st == TTSH_OK; ++i) st = run_row(d, ttsh::K_ROW_STEP, s);
+  cudaEventRecord(ev[1], s);
+  cudaEventRecord(ev[2], s);
+  for (int i = 0; i < iters && st == TTSH_OK; ++i) st = run_col(d, ttsh::K_COL_STEP, s);
+  cudaEventRecord(ev[3], s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  float t0 = 0.f, t1 = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[2], ev[3]);
+  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  if (st != TTSH_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "kernel timing");
+  ms[0] = t0 / iters;
+  ms[1] = t1 / iters;
+  // restore the state and rebuild the inverse-transformed fields from it
+  TTSH_CUDA(cudaMemcpyAsync(d->dev.what, save, wbytes, cudaMemcpyDeviceToDevice, s), "restore state");
+  TTSH_CUDA(cudaMemcpyAsync(d->dev.vmean, save + wbytes, 64, cudaMemcpyDeviceToDevice, s), "restore mean");
+  if ((st = run_col(d, ttsh::K_COL_PROLOGUE, s)) != TTSH_OK) return st;
+  return sync(d, "time_kernels");
+}
+
+ttsh_status ttsh_synchronize(ttsh_domain* d) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  return sync(d, "synchronize");
+}
+
+int64_t ttsh_step_count(const ttsh_domain* d) { return d ? d->steps : -1; }
+
+const char* ttsh_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

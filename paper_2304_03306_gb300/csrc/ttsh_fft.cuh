@@ -1,0 +1,183 @@
+// ttsh_fft.cuh - shared-memory FFT building blocks for the sm_103a solver kernels.
+//
+// The solver's transforms are the unitary DFT pair of Appendix D, applied separably: real
+// row transforms (length N, done as N/2-point complex transforms plus a twiddle pass) and
+// complex column transforms (length N).  Everything here is un-normalised; the kernels
+// apply the 1/N factors where the update needs them.
+//
+// Transform engine: in-place Stockham autosort with radix-PE register butterflies.  Each
+// transform of length L is owned by L/PE threads; in every stage a thread loads PE values
+// (PE/R butterflies of radix R), all threads synchronise, each applies the inter-stage
+// twiddles from a table of W_N^m = exp(-2 pi i m / N), an R-point DFT in registers
+// (radix-2 decimation in frequency, output in bit-reversed register order) and writes the
+// results to their Stockham positions.  Shared memory is padded by one slot every PE
+// elements so that the stride-PE writes of the first stage hit distinct banks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ttsh {
+
+template <typename T>
+struct cplx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> mk(T x, T y) {
+  cplx<T> r;
+  r.x = x;
+  r.y = y;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ cplx<T> operator*(cplx<T> a, T s) { return mk(a.x * s, a.y * s); }
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> conjg(cplx<T> a) { return mk(a.x, -a.y); }
+// i * a
+template <typename T>
+__device__ __forceinline__ cplx<T> mul_i(cplx<T> a) { return mk(-a.y, a.x); }
+
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+// Padded shared-memory index: one spare slot every 2^PS elements.
+template <int PS>
+__device__ __forceinline__ int padi(int i) { return i + (i >> PS); }
+template <int L, int PS>
+__host__ __device__ constexpr int padded_len() { return L + (L >> PS); }
+
+template <int R>
+__device__ __forceinline__ constexpr int bitrev(int i) {
+  int r = 0;
+  for (int b = 1; b < R; b <<= 1) {
+    r = (r << 1) | (i & 1);
+    i >>= 1;
+  }
+  return r;
+}
+
+// cos(2 pi j / 16) for j = 0..4 (exact decimal expansions of cos 0, cos pi/8, cos pi/4,
+// cos 3pi/8, cos pi/2); other angles follow by symmetry.
+__device__ __forceinline__ constexpr double cos16(int j) {
+  return j == 0 ? 1.0
+       : j == 1 ? 0.92387953251128675612818318939678828682241662586364
+       : j == 2 ? 0.70710678118654752440084436210484903928483593768847
+       : j == 3 ? 0.38268343236508977172845998403039886676134456248563
+       : 0.0;
+}
+
+// d * exp(DIR * 2 pi i j / 16), j in [0, 8), DIR = -1 (forward) or +1 (inverse).
+template <typename T, int DIR>
+__device__ __forceinline__ cplx<T> rot16(cplx<T> d, int j) {
+  if (j == 0) return d;
+  if (j == 4) return DIR > 0 ? mul_i(d) : mk(d.y, -d.x);
+  const T c = (T)(j <= 4 ? cos16(j) : -cos16(8 - j));
+  const T s = (T)(DIR) * (T)(j <= 4 ? cos16(4 - j) : cos16(j - 4));
+  return mk(d.x * c - d.y * s, d.x * s + d.y * c);
+}
+
+// In-register R-point DFT (R <= 16), sign DIR.  Radix-2 decimation in frequency: on exit
+// v[bitrev(k)] holds X[k].
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void dft_reg(cplx<T>* v) {
+#pragma unroll
+  for (int half = R / 2; half >= 1; half >>= 1) {
+#pragma unroll
+    for (int blk = 0; blk < R; blk += 2 * half) {
+#pragma unroll
+      for (int i = 0; i < half; ++i) {
+        const cplx<T> a = v[blk + i];
+        const cplx<T> b = v[blk + i + half];
+        v[blk + i] = a + b;
+        v[blk + i + half] = rot16<T, DIR>(a - b, i * (16 / (2 * half)));
+      }
+    }
+  }
+}
+
+// Twiddle W_N^idx (forward sign) or its conjugate.
+template <typename T, int DIR>
+__device__ __forceinline__ cplx<T> twiddle(const cplx<T>* __restrict__ tw, int idx) {
+  cplx<T> w = tw[idx];
+  if (DIR > 0) w.y = -w.y;
+  return w;
+}
+
+// One Stockham stage of radix R on a length-L transform at buf (padded), current
+// sub-transform length Ns.  j: this thread's index among the L/PE owners.
+template <typename T, int L, int PE, int R, int Ns, int DIR, int PS, int TWN>
+__device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
+                                               const cplx<T>* __restrict__ tw) {
+  constexpr int TT = L / PE;
+  constexpr int NB = PE / R;
+  cplx<T> v[NB][R];
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int q = j + b * TT;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = buf[padi<PS>(q + r * (L / R))];
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int q = j + b * TT;
+      const int k = q & (Ns - 1);
+      if (Ns > 1) {
+        constexpr int stride = TWN / (Ns * R);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], twiddle<T, DIR>(tw, r * k * stride));
+      }
+      dft_reg<T, R, DIR>(v[b]);
+      const int base = (q - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[padi<PS>(base + r * Ns)] = v[b][bitrev<R>(r)];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int L, int PE, int Ns, int DIR, int PS, int TWN>
+__device__ __forceinline__ void stockham_all(cplx<T>* buf, int j, bool active,
+                                             const cplx<T>* __restrict__ tw) {
+  if constexpr (Ns < L) {
+    constexpr int R = (L / Ns < PE) ? (L / Ns) : PE;
+    stockham_stage<T, L, PE, R, Ns, DIR, PS, TWN>(buf, j, active, tw);
+    stockham_all<T, L, PE, Ns * R, DIR, PS, TWN>(buf, j, active, tw);
+  }
+}
+
+// B transforms of length L laid out at sm + b * LP (padded), all threads of the block
+// participate (NT threads).  TWN: length of the twiddle table (a multiple of L).
+// Starts and ends with a block barrier.
+template <typename T, int L, int PE, int DIR, int NT, int TWN>
+__device__ __forceinline__ void fft_batch(cplx<T>* sm, int B, const cplx<T>* __restrict__ tw) {
+  constexpr int PS = ilog2(PE);
+  constexpr int LP = padded_len<L, PS>();
+  constexpr int TT = L / PE;
+  static_assert(NT % TT == 0, "block size must be a multiple of the threads per transform");
+  constexpr int PER = NT / TT;
+  const int j = threadIdx.x % TT;
+  const int slot = threadIdx.x / TT;
+  __syncthreads();
+  for (int c0 = 0; c0 < B; c0 += PER) {
+    const int b = c0 + slot;
+    const bool active = b < B;
+    stockham_all<T, L, PE, 1, DIR, PS, TWN>(sm + (active ? b : 0) * LP, j, active, tw);
+  }
+}
+
+}  // namespace ttsh

@@ -1,0 +1,54 @@
+// ttsh_ops.h - precision-erased launch interface between the host runtime (ttsh_api.cu)
+// and the per-precision kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ttsh {
+
+// Device pointers and constants of one domain, independent of the arithmetic type.
+struct DomainDev {
+  void* what;      // omega^ half-spectrum, H x NK complex
+  void* vmean;     // v^(0), 2 reals
+  void* K;         // processed mask, N x N reals
+  void* G;         // [4][H][N] complex
+  void* Rr;        // [3][H][N] complex
+  void* tw;        // N complex twiddles W_N^m
+  double* real;    // [3][N][N] double staging
+  double* part;    // row-block diagnostic partials
+  double* colhist; // H x (N/4 + 1) spectrum partials
+  int* bad;        // non-finite counter
+  double* out;     // reduced diagnostics (8 doubles) + spectrum bins
+  double a, b, lam, gv, gw, dx, dt;
+  double cx, cy;   // centre for the order parameter
+  int n;
+};
+
+enum { K_ROW_STEP = 0, K_ROW_FWD_VEL = 1, K_ROW_FWD_MASK = 2, K_ROW_INV_FIELDS = 3,
+       K_ROW_INV_MASK = 4, K_ROW_INV_DIAG = 5 };
+enum { K_COL_STEP = 0, K_COL_PROLOGUE = 1, K_COL_PROJECT = 2, K_COL_MASK = 3 };
+
+using RowFn = cudaError_t (*)(int kind, const DomainDev&, cudaStream_t);
+using ColFn = cudaError_t (*)(int mode, const DomainDev&, cudaStream_t);
+using SpecFn = cudaError_t (*)(const DomainDev&, int nbins, cudaStream_t);
+using BlocksFn = int (*)(int kind);
+
+struct SizeOps {
+  RowFn row;
+  ColFn col;
+  SpecFn spec;
+  BlocksFn row_blocks;   // grid size of a row kernel kind (number of diagnostic partials)
+};
+
+// Per translation unit registries; return false if the TU does not hold size n.
+bool ops_f32_small(int n, SizeOps* o);
+bool ops_f32_large(int n, SizeOps* o);
+bool ops_f64_small(int n, SizeOps* o);
+bool ops_f64_large(int n, SizeOps* o);
+
+cudaError_t launch_diag_reduce(const double* part, int nblocks, double* out, cudaStream_t s);
+cudaError_t launch_spectrum_reduce(const double* colhist, int ncols, int nbins, double scale,
+                                   double* out, cudaStream_t s);
+
+}  // namespace ttsh

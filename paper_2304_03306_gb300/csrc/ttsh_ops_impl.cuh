@@ -1,0 +1,131 @@
+// ttsh_ops_impl.cuh - template launchers; included by the per-precision translation units,
+// each of which defines TTSH_T (float or double), TTSH_REGISTRY (function name) and
+// TTSH_SIZES (an X-macro list of the grid sizes it instantiates).
+#pragma once
+
+#include <atomic>
+
+#include "ttsh_kernels.cuh"
+#include "ttsh_ops.h"
+
+namespace ttsh {
+
+template <typename T>
+static Args<T> make_args(const DomainDev& d) {
+  Args<T> a;
+  a.what = static_cast<cplx<T>*>(d.what);
+  a.vmean = static_cast<T*>(d.vmean);
+  a.K = static_cast<T*>(d.K);
+  a.G = static_cast<cplx<T>*>(d.G);
+  a.Rr = static_cast<cplx<T>*>(d.Rr);
+  a.tw = static_cast<const cplx<T>*>(d.tw);
+  a.real = d.real;
+  a.part = d.part;
+  const double dk = 2.0 * 3.14159265358979323846264338327950288 / ((double)d.n * d.dx);
+  a.a = (T)d.a;
+  a.b = (T)d.b;
+  a.lam = (T)d.lam;
+  a.gv = (T)d.gv;
+  a.gw = (T)d.gw;
+  a.dt = (T)d.dt;
+  a.dk = (T)dk;
+  a.mean_decay = (T)exp((d.a - 1.0) * d.dt);
+  a.dx = d.dx;
+  a.cx = d.cx;
+  a.cy = d.cy;
+  return a;
+}
+
+template <typename K>
+static cudaError_t set_smem(K kernel, int bytes, std::atomic<int>& done) {
+  if (done.load(std::memory_order_acquire)) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.store(1, std::memory_order_release);
+  return e;
+}
+
+template <typename T, int N, int KIND>
+static cudaError_t launch_row_kind(const DomainDev& d, cudaStream_t s) {
+  using Cfg = RowCfg<T, N, KIND>;
+  static std::atomic<int> done{0};
+  cudaError_t e = set_smem(row_kernel<T, N, KIND>, Cfg::SMEM, done);
+  if (e != cudaSuccess) return e;
+  row_kernel<T, N, KIND><<<N / Cfg::R, Cfg::NT, Cfg::SMEM, s>>>(make_args<T>(d));
+  return cudaGetLastError();
+}
+
+template <typename T, int N, int MODE>
+static cudaError_t launch_col_mode(const DomainDev& d, cudaStream_t s) {
+  using Cfg = ColCfg<T, N, MODE>;
+  static std::atomic<int> done{0};
+  cudaError_t e = set_smem(col_kernel<T, N, MODE>, Cfg::SMEM, done);
+  if (e != cudaSuccess) return e;
+  col_kernel<T, N, MODE><<<Cfg::H, Cfg::NT, Cfg::SMEM, s>>>(make_args<T>(d));
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+static cudaError_t launch_row(int kind, const DomainDev& d, cudaStream_t s) {
+  switch (kind) {
+    case K_ROW_STEP: return launch_row_kind<T, N, ROW_STEP>(d, s);
+    case K_ROW_FWD_VEL: return launch_row_kind<T, N, ROW_FWD_VEL>(d, s);
+    case K_ROW_FWD_MASK: return launch_row_kind<T, N, ROW_FWD_MASK>(d, s);
+    case K_ROW_INV_FIELDS: return launch_row_kind<T, N, ROW_INV_FIELDS>(d, s);
+    case K_ROW_INV_MASK: return launch_row_kind<T, N, ROW_INV_MASK>(d, s);
+    case K_ROW_INV_DIAG: return launch_row_kind<T, N, ROW_INV_DIAG>(d, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int N>
+static int row_blocks(int kind) {
+  switch (kind) {
+    case K_ROW_STEP: return N / RowCfg<T, N, ROW_STEP>::R;
+    case K_ROW_FWD_VEL: return N / RowCfg<T, N, ROW_FWD_VEL>::R;
+    case K_ROW_FWD_MASK: return N / RowCfg<T, N, ROW_FWD_MASK>::R;
+    case K_ROW_INV_FIELDS: return N / RowCfg<T, N, ROW_INV_FIELDS>::R;
+    case K_ROW_INV_MASK: return N / RowCfg<T, N, ROW_INV_MASK>::R;
+    case K_ROW_INV_DIAG: return N / RowCfg<T, N, ROW_INV_DIAG>::R;
+  }
+  return 0;
+}
+
+template <typename T, int N>
+static cudaError_t launch_col(int mode, const DomainDev& d, cudaStream_t s) {
+  switch (mode) {
+    case K_COL_STEP: return launch_col_mode<T, N, COL_STEP>(d, s);
+    case K_COL_PROLOGUE: return launch_col_mode<T, N, COL_PROLOGUE>(d, s);
+    case K_COL_PROJECT: return launch_col_mode<T, N, COL_PROJECT>(d, s);
+    case K_COL_MASK: return launch_col_mode<T, N, COL_MASK>(d, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, int N>
+static cudaError_t launch_spec(const DomainDev& d, int nbins, cudaStream_t s) {
+  constexpr int H = N / 4 + 1;
+  spectrum_col_kernel<T, N><<<(H + 127) / 128, 128, 0, s>>>(make_args<T>(d), nbins, d.colhist, d.bad);
+  return cudaGetLastError();
+}
+
+template <typename T, int N>
+static SizeOps make_ops() {
+  SizeOps o;
+  o.row = &launch_row<T, N>;
+  o.col = &launch_col<T, N>;
+  o.spec = &launch_spec<T, N>;
+  o.row_blocks = &row_blocks<T, N>;
+  return o;
+}
+
+bool TTSH_REGISTRY(int n, SizeOps* o) {
+  switch (n) {
+#define X(NN) \
+  case NN: *o = make_ops<TTSH_T, NN>(); return true;
+    TTSH_SIZES
+#undef X
+  }
+  return false;
+}
+
+}  // namespace ttsh

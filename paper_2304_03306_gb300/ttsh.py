@@ -1,0 +1,261 @@
+"""Thin ctypes binding of the C ABI in include/ttsh.h (libttsh.so, built for sm_103a).
+
+Functions carry the C entry points' names and only marshal arguments: every arithmetic
+step of the solver runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library is missing or cannot be loaded the first call raises.
+
+Host arrays are numpy float64 / uint8, C-contiguous, indexed [y][x].  Device pointers and
+streams are plain integers (e.g. ``tensor.data_ptr()``, ``torch.cuda.current_stream().cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libttsh.so")
+
+TTSH_OK, TTSH_E_INVALID, TTSH_E_OOM, TTSH_E_CUDA, TTSH_E_TIMEOUT, TTSH_E_NONFINITE, \
+    TTSH_E_UNSUPPORTED = range(7)
+_STATUS_NAMES = ["OK", "INVALID", "OOM", "CUDA", "TIMEOUT", "NONFINITE", "UNSUPPORTED"]
+
+
+class TTSHError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        name = _STATUS_NAMES[status] if 0 <= status < len(_STATUS_NAMES) else str(status)
+        super().__init__(f"TTSH_E_{name}: {message}")
+        self.status = status
+
+
+class ttsh_params(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("gamma_v", ctypes.c_double), ("gamma_w", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+                ("n", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class ttsh_diag(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("enstrophy", ctypes.c_double),
+                ("psi", ctypes.c_double), ("mean_vx", ctypes.c_double),
+                ("mean_vy", ctypes.c_double), ("step", ctypes.c_int64),
+                ("nonfinite", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libttsh.so once; raise if it is absent (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2304_03306_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    sigs = {
+        "ttsh_default_params": (None, [ctypes.POINTER(ttsh_params)]),
+        "ttsh_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(ttsh_params)]),
+        "ttsh_create_domain": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(ttsh_params),
+                                              _P, _P, ctypes.POINTER(_P)]),
+        "ttsh_destroy_domain": (None, [_P]),
+        "ttsh_set_stream": (ctypes.c_int, [_P, _P]),
+        "ttsh_set_velocity": (ctypes.c_int, [_P, _D, _D]),
+        "ttsh_set_velocity_device": (ctypes.c_int, [_P, _P, _P]),
+        "ttsh_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+        "ttsh_get_fields": (ctypes.c_int, [_P, _D, _D, _D]),
+        "ttsh_get_mask": (ctypes.c_int, [_P, _D]),
+        "ttsh_get_spectral_state": (ctypes.c_int, [_P, _D, _D]),
+        "ttsh_set_spectral_state": (ctypes.c_int, [_P, _D, _D]),
+        "ttsh_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(ttsh_diag), _D, ctypes.c_int32, _D]),
+        "ttsh_synchronize": (ctypes.c_int, [_P]),
+        "ttsh_time_kernels": (ctypes.c_int, [_P, ctypes.c_int32, _D]),
+        "ttsh_step_count": (ctypes.c_int64, [_P]),
+        "ttsh_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != TTSH_OK:
+        raise TTSHError(status, ttsh_last_error())
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != (n, n):
+        raise ValueError(f"expected shape {(n, n)}, got {a.shape}")
+    return a
+
+
+def ttsh_last_error() -> str:
+    return load_library().ttsh_last_error().decode()
+
+
+def ttsh_default_params(n: int = 8192, dx: float = 0.005, precision: int = 32, **kw) -> ttsh_params:
+    p = ttsh_params()
+    load_library().ttsh_default_params(ctypes.byref(p))
+    p.n, p.dx, p.precision = n, dx, precision
+    for k, v in kw.items():
+        setattr(p, "lambda_" if k in ("lam", "lambda") else k, v)
+    return p
+
+
+def ttsh_workspace_bytes(p: ttsh_params) -> int:
+    return int(load_library().ttsh_workspace_bytes(ctypes.byref(p)))
+
+
+def ttsh_create_domain(mask, p: ttsh_params, workspace: int | None = None, stream: int | None = None):
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    if m.shape != (p.n, p.n):
+        raise ValueError(f"mask must have shape {(p.n, p.n)}")
+    h = _P()
+    _check(load_library().ttsh_create_domain(m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                             ctypes.byref(p), workspace, stream, ctypes.byref(h)))
+    return h
+
+
+def ttsh_destroy_domain(h):
+    load_library().ttsh_destroy_domain(h)
+
+
+def ttsh_set_stream(h, stream: int | None):
+    _check(load_library().ttsh_set_stream(h, stream))
+
+
+def ttsh_set_velocity(h, vx, vy, n: int):
+    vx, vy = _f64(vx, n), _f64(vy, n)
+    _check(load_library().ttsh_set_velocity(h, _dptr(vx), _dptr(vy)))
+
+
+def ttsh_set_velocity_device(h, vx_ptr: int, vy_ptr: int):
+    _check(load_library().ttsh_set_velocity_device(h, vx_ptr, vy_ptr))
+
+
+def ttsh_step(h, nsteps: int):
+    _check(load_library().ttsh_step(h, int(nsteps)))
+
+
+def ttsh_get_fields(h, n: int):
+    vx, vy, w = (np.empty((n, n)) for _ in range(3))
+    _check(load_library().ttsh_get_fields(h, _dptr(vx), _dptr(vy), _dptr(w)))
+    return vx, vy, w
+
+
+def ttsh_get_mask(h, n: int):
+    K = np.empty((n, n))
+    _check(load_library().ttsh_get_mask(h, _dptr(K)))
+    return K
+
+
+def ttsh_get_spectral_state(h, n: int):
+    M = n // 4
+    buf = np.empty((M + 1, 2 * M + 1, 2))
+    v0 = np.empty(2)
+    _check(load_library().ttsh_get_spectral_state(h, _dptr(buf), _dptr(v0)))
+    return buf[..., 0] + 1j * buf[..., 1], v0
+
+
+def ttsh_set_spectral_state(h, w_hat, v0):
+    buf = np.ascontiguousarray(np.stack([np.real(w_hat), np.imag(w_hat)], axis=-1), dtype=np.float64)
+    v = np.ascontiguousarray(v0, dtype=np.float64)
+    _check(load_library().ttsh_set_spectral_state(h, _dptr(buf), _dptr(v)))
+
+
+def ttsh_diagnostics(h, nbins: int = 0, centre=(0.0, 0.0)) -> dict:
+    d = ttsh_diag()
+    spec = np.zeros(max(nbins, 1))
+    c = np.ascontiguousarray(centre, dtype=np.float64)
+    st = load_library().ttsh_diagnostics(h, ctypes.byref(d), _dptr(spec) if nbins else None,
+                                         int(nbins), _dptr(c))
+    if st not in (TTSH_OK, TTSH_E_NONFINITE):
+        _check(st)
+    out = {k: getattr(d, k) for k, _ in ttsh_diag._fields_ if k != "reserved"}
+    out["status"] = st
+    if nbins:
+        out["spectrum"] = spec[:nbins]
+    return out
+
+
+def ttsh_time_kernels(h, iters: int):
+    ms = np.zeros(2)
+    _check(load_library().ttsh_time_kernels(h, int(iters), _dptr(ms)))
+    return float(ms[0]), float(ms[1])
+
+
+def ttsh_synchronize(h):
+    _check(load_library().ttsh_synchronize(h))
+
+
+def ttsh_step_count(h) -> int:
+    return int(load_library().ttsh_step_count(h))
+
+
+class Domain:
+    """Convenience owner of one ttsh_domain handle."""
+
+    def __init__(self, mask, n: int, dx: float, precision: int = 32, workspace: int | None = None,
+                 stream: int | None = None, **coef):
+        self.n = n
+        self.params = ttsh_default_params(n=n, dx=dx, precision=precision, **coef)
+        self.h = ttsh_create_domain(mask, self.params, workspace, stream)
+
+    def close(self):
+        if self.h:
+            ttsh_destroy_domain(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_velocity(self, vx, vy):
+        ttsh_set_velocity(self.h, vx, vy, self.n)
+
+    def set_velocity_device(self, vx_ptr: int, vy_ptr: int):
+        ttsh_set_velocity_device(self.h, vx_ptr, vy_ptr)
+
+    def set_stream(self, stream: int | None):
+        ttsh_set_stream(self.h, stream)
+
+    def step(self, nsteps: int):
+        ttsh_step(self.h, nsteps)
+
+    def fields(self):
+        return ttsh_get_fields(self.h, self.n)
+
+    def mask(self):
+        return ttsh_get_mask(self.h, self.n)
+
+    def spectral_state(self):
+        return ttsh_get_spectral_state(self.h, self.n)
+
+    def set_spectral_state(self, w_hat, v0):
+        ttsh_set_spectral_state(self.h, w_hat, v0)
+
+    def diagnostics(self, nbins: int = 0, centre=(0.0, 0.0)):
+        return ttsh_diagnostics(self.h, nbins, centre)
+
+    def synchronize(self):
+        ttsh_synchronize(self.h)
+
+    def time_kernels(self, iters: int):
+        """Mean (row pass, column pass) launch durations in ms, state restored afterwards."""
+        return ttsh_time_kernels(self.h, iters)
+
+    @property
+    def steps(self) -> int:
+        return ttsh_step_count(self.h)

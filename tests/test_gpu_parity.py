@@ -1,0 +1,288 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative L2 over the whole field unless stated):
+  FP64 domains: 1e-12 after up to 100 steps (rounding-order differences only);
+  FP32 domains: 1e-5 after 100 steps (FP32 unit round-off 6e-8 times the transform depth
+  and the number of steps, well inside the bound).
+Exact checks: omega^(0) = 0, modes outside the 1/2-rule disc are 0, the stored mx = 0
+column is Hermitian, checkpoint/resume and graph replay are bit-identical.
+"""
+import numpy as np
+import pytest
+
+import ttsh_inputs as ti
+from oracle import ttsh_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def T():
+    from paper_2304_03306_gb300 import build, ttsh
+    build.build()
+    ttsh.load_library()
+    return ttsh
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def half_layout(w_hat):
+    """Oracle full FFT-ordered spectrum [ky][kx] -> the library's [mx][j] half layout."""
+    n = w_hat.shape[0]
+    M = n // 4
+    NK = 2 * M + 1
+    ky = np.array([j if j <= M else j - NK for j in range(NK)])
+    return w_hat[np.ix_(ky % n, np.arange(M + 1))].T
+
+
+def setup(T, n, dx, radius, prec, seed, amp=0.01, mask=None):
+    if mask is None:
+        mask = ti.circle_mask(n, dx, radius)
+    p = O.Params(n=n, dx=dx)
+    dom = T.Domain(mask, n, dx, precision=prec)
+    vx, vy = ti.noise_velocity(mask, seed, amp)
+    dom.set_velocity(vx, vy)
+    K = O.process_mask(mask)
+    s = O.project_velocity(vx, vy, p)
+    return dom, p, K, s
+
+
+def check_fields(dom, s, tol):
+    vx, vy, w = dom.fields()
+    assert rel(w, O.vorticity(s)) <= tol
+    assert rel(np.stack([vx, vy]), np.stack([s.vx, s.vy])) <= tol
+
+
+# ------------------------------------------------------------------- Algorithm 2
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("n,dx,shape", [(16, 1.0, "circle"), (64, 0.25, "circle"),
+                                        (256, 0.08, "dumbbell"), (512, 0.04, "circle")])
+def test_mask_matches_oracle(T, prec, n, dx, shape):
+    R = 5.2 if shape == "circle" else 3.0
+    mask = ti.circle_mask(n, dx, R) if shape == "circle" else ti.dumbbell_mask(n, dx, R, 1.5 * R)
+    dom = T.Domain(mask, n, dx, precision=prec)
+    K = dom.mask()
+    Ko = O.process_mask(mask)
+    assert np.abs(K - Ko).max() <= (1e-13 if prec == 64 else 2e-6)
+    assert K.min() >= 0.0
+
+
+# --------------------------------------------------------- initial-state projection
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("n,dx", [(16, 1.0), (32, 0.5), (128, 0.125)])
+def test_projection_matches_oracle(T, prec, n, dx):
+    dom, p, K, s = setup(T, n, dx, 5.0, prec, 3, amp=0.5)
+    check_fields(dom, s, TOL[prec] / 10)
+    w_hat, v0 = dom.spectral_state()
+    ref = half_layout(s.w_hat)
+    assert rel(w_hat, ref) <= TOL[prec] / 10
+    np.testing.assert_allclose(v0, [np.sum(s.vx) / n, np.sum(s.vy) / n], rtol=TOL[prec],
+                               atol=1e-15 * n)
+
+
+# ---------------------------------------------------------------- Algorithm 1 parity
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("n,dx,R,steps", [(16, 1.0, 5.0, 100), (32, 0.5, 5.2, 100),
+                                          (64, 0.25, 5.2, 100), (128, 0.16, 5.3, 100),
+                                          (256, 0.08, 5.6, 100)])
+def test_steps_match_oracle(T, prec, n, dx, R, steps):
+    dom, p, K, s = setup(T, n, dx, R, prec, 1, amp=0.3)
+    dom.step(steps)
+    s = O.run(s, K, p, steps)
+    check_fields(dom, s, TOL[prec])
+    w_hat, v0 = dom.spectral_state()
+    assert rel(w_hat, half_layout(s.w_hat)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_bench_workload_512(T, prec):
+    """The timed workload's configuration (512^2 circle, dx = 0.04, R = 5.4, noise 0.01,
+    seed 2) over 100 steps, with the step loop replayed as a CUDA graph."""
+    w = ti.WORKLOADS["circle512"]
+    dom, p, K, s = setup(T, w["n"], w["dx"], w["radius"], prec, w["seed"], amp=0.01)
+    dom.step(100)
+    s = O.run(s, K, p, 100)
+    check_fields(dom, s, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_2048_few_steps(T, prec):
+    w = ti.WORKLOADS["circle2048_turbulent"]
+    dom, p, K, s = setup(T, w["n"], w["dx"], w["radius"], prec, w["seed"], amp=0.3)
+    dom.step(3)
+    s = O.run(s, K, p, 3)
+    check_fields(dom, s, TOL[prec])
+
+
+# --------------------------------------------------------- closed forms at any size
+
+@pytest.mark.parametrize("prec,n", [(32, 16), (32, 8192), (64, 16), (64, 4096), (32, 1024)])
+def test_linear_single_mode_closed_form(T, prec, n):
+    """b = lambda = 0, K = 0: a mode grows by exp[(a - (1 - k^2)^2) dt] per step exactly."""
+    dx = 16.0 / n
+    mask = np.zeros((n, n), np.uint8)
+    dom = T.Domain(mask, n, dx, precision=prec, b=0.0, lam=0.0)
+    X, Y = ti.grid_coords(n, dx)
+    dk = 2 * np.pi / (n * dx)
+    m = (2, 3)
+    kx, ky = dk * m[0], dk * m[1]
+    th = kx * X + ky * Y + 0.3
+    A = 0.4
+    vx, vy = -A * ky * np.sin(th), A * kx * np.sin(th)
+    w0 = A * (kx * kx + ky * ky) * np.cos(th)
+    dom.set_velocity(vx, vy)
+    steps = 150
+    dom.step(steps)
+    g = np.exp((0.5 - (1 - kx * kx - ky * ky) ** 2) * 0.01) ** steps
+    gvx, gvy, gw = dom.fields()
+    tol = 1e-12 if prec == 64 else 2e-5
+    assert rel(gw, g * w0) <= tol
+    assert rel(np.stack([gvx, gvy]), g * np.stack([vx, vy])) <= tol
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_uniform_mask_closed_form(T, prec):
+    """K_naive = 1 everywhere gives K = 1; with b = lambda = 0 each mode is multiplied by
+    exp(sigma dt)(1 - (gamma_v + gamma_w) dt) and the mean flow by exp((a-1)dt)(1 - gamma_v dt)."""
+    n, dx = 64, 0.25
+    mask = np.ones((n, n), np.uint8)
+    dom = T.Domain(mask, n, dx, precision=prec, b=0.0, lam=0.0)
+    X, Y = ti.grid_coords(n, dx)
+    dk = 2 * np.pi / (n * dx)
+    kx, ky = dk * 1, dk * 2
+    th = kx * X + ky * Y
+    vx, vy = -0.2 * ky * np.sin(th) + 0.05, 0.2 * kx * np.sin(th) - 0.03
+    dom.set_velocity(vx, vy)
+    dom.step(5)
+    g = (np.exp((0.5 - (1 - kx * kx - ky * ky) ** 2) * 0.01) * (1 - 44 * 0.01)) ** 5
+    gm = (np.exp(-0.5 * 0.01) * (1 - 40 * 0.01)) ** 5
+    gvx, gvy, _ = dom.fields()
+    tol = 1e-12 if prec == 64 else 1e-5
+    assert rel(gvx, g * (vx - 0.05) + gm * 0.05) <= tol
+    assert rel(gvy, g * (vy + 0.03) - gm * 0.03) <= tol
+
+
+# ------------------------------------------------------------------ invariants
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_invariants_of_gpu_state(T, prec):
+    n, dx = 128, 0.16
+    dom, p, K, s = setup(T, n, dx, 5.3, prec, 5, amp=0.3)
+    dom.step(40)
+    w_hat, _ = dom.spectral_state()
+    M = n // 4
+    NK = 2 * M + 1
+    assert w_hat[0, 0] == 0                                          # P5 exactly
+    mx = np.arange(M + 1)[:, None]
+    my = np.array([j if j <= M else j - NK for j in range(NK)])[None, :]
+    assert np.all(w_hat[(mx * mx + my * my) > M * M] == 0)           # 1/2 rule exactly
+    col0 = w_hat[0]
+    assert np.all(col0[1:M + 1] == np.conj(col0[NK - 1:M:-1]))      # Hermitian exactly
+    vx, vy, _ = dom.fields()
+    KX, KY, _ = O.wavenumbers(p)
+    Vx, Vy = np.fft.fft2(vx, norm="ortho"), np.fft.fft2(vy, norm="ortho")
+    div = np.abs(KX * Vx + KY * Vy).max() / (np.abs(np.hypot(KX, KY)) * np.hypot(np.abs(Vx), np.abs(Vy))).max()
+    assert div <= (1e-13 if prec == 64 else 1e-6)                   # P4
+
+
+# ------------------------------------------------------------------ diagnostics
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_diagnostics_match_oracle(T, prec):
+    n, dx = 128, 0.16
+    dom, p, K, s = setup(T, n, dx, 5.3, prec, 6, amp=0.3)
+    dom.step(20)
+    s = O.run(s, K, p, 20)
+    nb = n // 4 + 1
+    d = dom.diagnostics(nbins=nb + 3, centre=(0.1, -0.05))
+    o = O.diagnostics(s, p, center=(0.1, -0.05), nbins=nb + 3)
+    tol = 1e-11 if prec == 64 else 2e-5
+    for k in ["energy", "enstrophy", "psi"]:
+        assert abs(d[k] - o[k]) <= tol * max(abs(o[k]), 1e-3), (k, d[k], o[k])
+    assert abs(d["mean_vx"] - o["mean_vx"]) <= 1e-6 and abs(d["mean_vy"] - o["mean_vy"]) <= 1e-6
+    assert rel(d["spectrum"], o["spectrum"]) <= tol
+    assert np.all(d["spectrum"][nb:] == 0)
+    assert d["spectrum"].sum() == pytest.approx(d["energy"], rel=1e-6 if prec == 32 else 1e-12)
+    assert d["nonfinite"] == 0 and d["status"] == T.TTSH_OK and d["step"] == 20
+    # a second call gives identical bits (fixed-order reductions)
+    d2 = dom.diagnostics(nbins=nb + 3, centre=(0.1, -0.05))
+    assert d2["energy"] == d["energy"] and np.array_equal(d2["spectrum"], d["spectrum"])
+
+
+def test_nonfinite_state_is_reported(T):
+    n = 32
+    dom, p, K, s = setup(T, n, 0.5, 5.0, 32, 1)
+    w_hat, v0 = dom.spectral_state()
+    w_hat[1, 1] = np.nan
+    dom.set_spectral_state(w_hat, v0)
+    d = dom.diagnostics()
+    assert d["status"] == T.TTSH_E_NONFINITE and d["nonfinite"] > 0
+
+
+# ------------------------------------------------------- checkpoint / graphs
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_checkpoint_resume_is_bit_exact(T, prec):
+    n, dx = 64, 0.25
+    mask = ti.circle_mask(n, dx, 5.2)
+    vx, vy = ti.noise_velocity(mask, 9, 0.3)
+    a = T.Domain(mask, n, dx, precision=prec)
+    a.set_velocity(vx, vy)
+    a.step(30)
+    w_hat, v0 = a.spectral_state()
+    a.step(170)
+    b = T.Domain(mask, n, dx, precision=prec)
+    b.set_spectral_state(w_hat, v0)
+    b.step(170)
+    wa, va = a.spectral_state()
+    wb, vb = b.spectral_state()
+    assert np.array_equal(wa, wb) and np.array_equal(va, vb)
+
+
+def test_graph_replay_equals_eager_launches(T):
+    n, dx = 64, 0.25
+    mask = ti.circle_mask(n, dx, 5.2)
+    vx, vy = ti.noise_velocity(mask, 4, 0.3)
+    a = T.Domain(mask, n, dx, precision=32)
+    b = T.Domain(mask, n, dx, precision=32)
+    a.set_velocity(vx, vy)
+    b.set_velocity(vx, vy)
+    a.step(300)
+    for _ in range(300):
+        b.step(1)
+    assert a.steps == b.steps == 300
+    assert np.array_equal(a.spectral_state()[0], b.spectral_state()[0])
+
+
+def test_fp64_8192_is_unsupported(T):
+    with pytest.raises(T.TTSHError) as e:
+        T.Domain(np.zeros((8192, 8192), np.uint8), 8192, 0.005, precision=64)
+    assert e.value.status == T.TTSH_E_UNSUPPORTED
+
+
+# ------------------------------------------------------------ D4 symmetry
+
+def test_rotation_symmetry_on_gpu(T):
+    n, dx = 64, 0.25
+    mask = ti.circle_mask(n, dx, 5.2)
+    vx, vy = ti.noise_velocity(mask, 13, 0.3)
+    iy, ix = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    sy, sx = (n - ix) % n, iy
+    rvx, rvy = -vy[sy, sx], vx[sy, sx]
+    a = T.Domain(mask, n, dx, precision=64)
+    b = T.Domain(mask, n, dx, precision=64)
+    a.set_velocity(vx, vy)
+    b.set_velocity(rvx, rvy)
+    a.step(60)
+    b.step(60)
+    ax, ay, aw = a.fields()
+    bx, by, bw = b.fields()
+    assert rel(np.stack([bx, by]), np.stack([-ay[sy, sx], ax[sy, sx]])) <= 1e-12
+    assert rel(bw, aw[sy, sx]) <= 1e-12
