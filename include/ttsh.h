@@ -154,6 +154,27 @@ ttsh_status ttsh_diagnostics(ttsh_domain* d, ttsh_diag* out, double* spectrum, i
  * iters must be in [1, 1000000]. */
 ttsh_status ttsh_time_kernels(ttsh_domain* d, int32_t iters, double* ms);
 
+/* Advance a caller-owned state by nsteps steps of Algorithm 1 without allocating any device
+ * memory (the paper has no counterpart: this is a library convenience).  It is meant for
+ * callers that cannot let a library call cudaMalloc - their device memory belongs to their
+ * own pool or fixed budget, or they cannot afford the device-wide synchronisation an
+ * allocation or free implies.  Inputs and outputs are the caller's device buffers, in the
+ * precision p->precision selects (float or double):
+ *   K      N*N mask values [y][x] (e.g. copied from ttsh_get_mask), read only;
+ *   w_hat  omega^ in the half-spectrum layout above, H*NK complex (re, im interleaved),
+ *          advanced in place;
+ *   v0     v^(0), 2 values, advanced in place.
+ * Scratch (inter-pass buffers, twiddle tables) lives in one fixed device array inside the
+ * library, sized for n <= 512 (about 7.4 MB, held by every GPU that loads the library until
+ * the process exits); n > 512 -> TTSH_E_INVALID, as are the parameter checks of
+ * ttsh_create_domain.  The first call on each device resolves that array's address and
+ * writes its twiddle tables (synchronous copies); make that first call before any stream
+ * capture.  All calls share the array, so calls that overlap on the GPU race: serialise
+ * them.  Kernels are issued on `stream` (NULL = legacy default) and the call returns without
+ * waiting for them. */
+ttsh_status ttsh_step_noalloc(const ttsh_params* p, const void* K, void* w_hat, void* v0,
+                              int64_t nsteps, void* stream);
+
 /* Block the host until the domain's stream is idle; reports deferred CUDA errors. */
 ttsh_status ttsh_synchronize(ttsh_domain* d);
 

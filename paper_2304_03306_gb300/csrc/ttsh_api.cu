@@ -214,6 +214,10 @@ __global__ void spectrum_reduce_kernel(const double* __restrict__ colhist, int n
   out[s] = acc * scale;
 }
 
+void set_last_error(const char* msg) { g_last_error = msg; }
+
+void set_last_error(const char* what, cudaError_t e) { cuda_fail(e, what); }
+
 cudaError_t launch_diag_reduce(const double* part, int nblocks, double* out, cudaStream_t s) {
   diag_reduce_kernel<<<1, 256, 0, s>>>(part, nblocks, out);
   return cudaGetLastError();

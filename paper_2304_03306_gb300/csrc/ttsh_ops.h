@@ -47,6 +47,11 @@ bool ops_f32_large(int n, SizeOps* o);
 bool ops_f64_small(int n, SizeOps* o);
 bool ops_f64_large(int n, SizeOps* o);
 
+// Record the calling thread's message for ttsh_last_error() (used by entry points defined
+// outside ttsh_api.cu).
+void set_last_error(const char* msg);
+void set_last_error(const char* what, cudaError_t e);
+
 cudaError_t launch_diag_reduce(const double* part, int nblocks, double* out, cudaStream_t s);
 cudaError_t launch_spectrum_reduce(const double* colhist, int ncols, int nbins, double scale,
                                    double* out, cudaStream_t s);

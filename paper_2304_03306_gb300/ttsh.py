@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH):
         "ttsh_synchronize": (ctypes.c_int, [_P]),
         "ttsh_time_kernels": (ctypes.c_int, [_P, ctypes.c_int32, _D]),
         "ttsh_step_count": (ctypes.c_int64, [_P]),
+        "ttsh_step_noalloc": (ctypes.c_int, [ctypes.POINTER(ttsh_params), _P, _P, _P, ctypes.c_int64, _P]),
         "ttsh_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sigs.items():
@@ -196,6 +197,13 @@ def ttsh_time_kernels(h, iters: int):
 
 def ttsh_synchronize(h):
     _check(load_library().ttsh_synchronize(h))
+
+
+def ttsh_step_noalloc(p: ttsh_params, K_ptr: int, w_hat_ptr: int, v0_ptr: int, nsteps: int,
+                      stream: int | None = None):
+    """Advance caller-owned device buffers (mask, half-spectrum state, mean flow) without the
+    library allocating device memory; n <= 512.  See include/ttsh.h."""
+    _check(load_library().ttsh_step_noalloc(ctypes.byref(p), K_ptr, w_hat_ptr, v0_ptr, int(nsteps), stream))
 
 
 def ttsh_step_count(h) -> int:
