@@ -8,10 +8,14 @@
 // Transform engine: in-place Stockham autosort with radix-PE register butterflies.  Each
 // transform of length L is owned by L/PE threads; in every stage a thread loads PE values
 // (PE/R butterflies of radix R), all threads synchronise, each applies the inter-stage
-// twiddles from a table of W_N^m = exp(-2 pi i m / N), an R-point DFT in registers
-// (radix-2 decimation in frequency, output in bit-reversed register order) and writes the
-// results to their Stockham positions.  Shared memory is padded by one slot every PE
-// elements so that the stride-PE writes of the first stage hit distinct banks.
+// twiddles, an R-point DFT in registers (radix-2 decimation in frequency, output in
+// bit-reversed register order) and writes the results to their Stockham positions.  Shared
+// memory is padded by one slot every PE elements so that the stride-PE writes of the first
+// stage hit distinct banks.
+//
+// Twiddles W_N^m = exp(-2 pi i m / N) come from two small shared-memory tables,
+// W_N^m = W_N^{(m >> S) 2^S} * W_N^{m mod 2^S} with 2^S ~ sqrt(N), filled once per block from
+// a correctly rounded global table; no stage waits on global memory.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -106,19 +110,68 @@ __device__ __forceinline__ void dft_reg(cplx<T>* v) {
   }
 }
 
-// Twiddle W_N^idx (forward sign) or its conjugate.
-template <typename T, int DIR>
-__device__ __forceinline__ cplx<T> twiddle(const cplx<T>* __restrict__ tw, int idx) {
-  cplx<T> w = tw[idx];
+// Two-level twiddle table in shared memory for W_TWN^m, m in [0, TWN).
+template <typename T, int TWN>
+struct TwTab {
+  static constexpr int LOG = ilog2(TWN);
+  static constexpr int SB = (LOG + 1) / 2;
+  static constexpr int NLO = 1 << SB;
+  static constexpr int NHI = TWN >> SB;
+  static constexpr int ENTRIES = NLO + NHI;
+  const cplx<T>* lo;   // W^i,          i < NLO
+  const cplx<T>* hi;   // W^(i * NLO),  i < NHI
+  __device__ __forceinline__ cplx<T> get(int m) const {
+    if constexpr (NHI == 1) {
+      return lo[m];
+    } else {
+      return cmul(hi[m >> SB], lo[m & (NLO - 1)]);
+    }
+  }
+  // Fill from the global table (all threads of the block; caller synchronises).
+  __device__ __forceinline__ static TwTab fill(cplx<T>* sm, const cplx<T>* __restrict__ tw, int tid, int nt) {
+    for (int i = tid; i < ENTRIES; i += nt) sm[i] = i < NLO ? tw[i] : tw[(i - NLO) * NLO];
+    TwTab t;
+    t.lo = sm;
+    t.hi = sm + NLO;
+    return t;
+  }
+};
+
+template <typename T, int DIR, typename TW>
+__device__ __forceinline__ cplx<T> twiddle(const TW& tw, int idx) {
+  cplx<T> w = tw.get(idx);
   if (DIR > 0) w.y = -w.y;
   return w;
+}
+
+// Asynchronous global -> shared copies (cp.async, completion tracked per thread).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  if constexpr (BYTES == 16) cp_async16(smem, gmem);
+  else if constexpr (BYTES == 8) cp_async8(smem, gmem);
+  else cp_async4(smem, gmem);
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
 }
 
 // One Stockham stage of radix R on a length-L transform at buf (padded), current
 // sub-transform length Ns.  j: this thread's index among the L/PE owners.
 template <typename T, int L, int PE, int R, int Ns, int DIR, int PS, int TWN>
 __device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
-                                               const cplx<T>* __restrict__ tw) {
+                                               const TwTab<T, TWN>& tw) {
   constexpr int TT = L / PE;
   constexpr int NB = PE / R;
   cplx<T> v[NB][R];
@@ -152,7 +205,7 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
 
 template <typename T, int L, int PE, int Ns, int DIR, int PS, int TWN>
 __device__ __forceinline__ void stockham_all(cplx<T>* buf, int j, bool active,
-                                             const cplx<T>* __restrict__ tw) {
+                                             const TwTab<T, TWN>& tw) {
   if constexpr (Ns < L) {
     constexpr int R = (L / Ns < PE) ? (L / Ns) : PE;
     stockham_stage<T, L, PE, R, Ns, DIR, PS, TWN>(buf, j, active, tw);
@@ -164,7 +217,7 @@ __device__ __forceinline__ void stockham_all(cplx<T>* buf, int j, bool active,
 // participate (NT threads).  TWN: length of the twiddle table (a multiple of L).
 // Starts and ends with a block barrier.
 template <typename T, int L, int PE, int DIR, int NT, int TWN>
-__device__ __forceinline__ void fft_batch(cplx<T>* sm, int B, const cplx<T>* __restrict__ tw) {
+__device__ __forceinline__ void fft_batch(cplx<T>* sm, int B, const TwTab<T, TWN>& tw) {
   constexpr int PS = ilog2(PE);
   constexpr int LP = padded_len<L, PS>();
   constexpr int TT = L / PE;

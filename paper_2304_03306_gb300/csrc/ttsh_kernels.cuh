@@ -21,7 +21,9 @@
 //     fields the next row pass needs.
 //
 // Inter-pass buffers are column-major, [field][mx][y], so the column pass streams whole
-// columns and the row pass reads/writes R consecutive y per column.
+// columns and the row pass reads/writes R consecutive y per column.  Every global input a
+// block needs is first staged into shared memory with cp.async (all copies in flight at
+// once, one wait), so the transform stages never wait on global memory.
 #pragma once
 
 #include "ttsh_fft.cuh"
@@ -50,10 +52,9 @@ enum RowKind { ROW_STEP = 0, ROW_FWD_VEL = 1, ROW_FWD_MASK = 2, ROW_INV_FIELDS =
 enum ColMode { COL_STEP = 0, COL_PROLOGUE = 1, COL_PROJECT = 2, COL_MASK = 3 };
 
 constexpr int kDiagQ = 5;   // per-block partials: sum|v|^2, sum w^2, sum|e_th.v|, sum|v|, #nonfinite
+constexpr int kSmemLimit = 220 * 1024;
 
-// Points per thread of the register butterflies.
-template <typename T>
-__host__ __device__ constexpr int points_per_thread() { return sizeof(T) == 4 ? 16 : 8; }
+__host__ __device__ constexpr int align16(int v) { return (v + 15) / 16 * 16; }
 
 template <int KIND> __host__ __device__ constexpr int row_inv_fields() {
   return KIND == ROW_STEP ? 5 : KIND == ROW_INV_FIELDS ? 3 : KIND == ROW_INV_DIAG ? 3
@@ -62,65 +63,111 @@ template <int KIND> __host__ __device__ constexpr int row_inv_fields() {
 template <int KIND> __host__ __device__ constexpr int row_fwd_fields() {
   return KIND == ROW_STEP ? 3 : KIND == ROW_FWD_VEL ? 2 : KIND == ROW_FWD_MASK ? 1 : 0;
 }
-template <int KIND> __host__ __device__ constexpr int row_max_fields() {
-  return cmax(row_inv_fields<KIND>(), row_fwd_fields<KIND>());
-}
 
-// Row-pass geometry: R rows per block, NT threads.
-template <typename T, int N, int KIND>
-struct RowCfg {
-  static constexpr int L = N / 2;
-  static constexpr int PE = cmin(points_per_thread<T>(), L);
+// Default tile shapes (the autotuner may pick others for the step kernels).
+template <typename T, int N>
+__host__ __device__ constexpr int default_rows() {
+  return sizeof(T) == 4 ? (N <= 1024 ? 4 : N == 2048 ? 2 : 1) : (N <= 1024 ? 2 : 1);
+}
+template <typename T, int N>
+__host__ __device__ constexpr int default_row_pe() { return sizeof(T) == 4 ? 16 : 8; }
+template <typename T, int N>
+__host__ __device__ constexpr int default_col_pe() { return sizeof(T) == 4 ? (N <= 1024 ? 8 : 16) : 8; }
+
+// Row-pass geometry and shared-memory plan.
+template <typename T, int N, int KIND, int R, int PEV>
+struct RowGeo {
+  static constexpr int L = N / 2, M = N / 4, H = M + 1;
+  static constexpr int PE = cmin(PEV, L);
   static constexpr int PS = ilog2(PE);
   static constexpr int LP = padded_len<L, PS>();
   static constexpr int TT = L / PE;
-  static constexpr int F = row_max_fields<KIND>();
-  static constexpr int bytes_per_row = F * LP * (int)sizeof(cplx<T>);
-  // Rows per block: up to 32 bytes of consecutive y per column segment (4 floats / 2
-  // doubles complex), fewer if the shared memory would exceed ~110 KB.
-  static constexpr int R0 = sizeof(T) == 4 ? 4 : 2;
-  static constexpr int R = (bytes_per_row * R0 <= 112 * 1024) ? R0
-                         : (bytes_per_row * (R0 / 2) <= 112 * 1024 && R0 > 1) ? R0 / 2 : 1;
-  static constexpr int NT = cmax(64, cmin(1024, cmax(1, F * R) * TT));
-  static constexpr int SMEM = bytes_per_row * R + kDiagQ * 1024 * 8 * (KIND == ROW_INV_DIAG);
+  static constexpr int FI = row_inv_fields<KIND>();
+  static constexpr int FF = row_fwd_fields<KIND>();
+  static constexpr int F = cmax(FI, FF);
+  static constexpr int NPL = FI == 0 ? 0 : (KIND == ROW_INV_MASK ? 1 : 4);   // G planes read
+  static constexpr int CB = (int)sizeof(cplx<T>);
+  static constexpr int TW_BYTES = align16(TwTab<T, N>::ENTRIES * CB);
+  static constexpr int BUF_BYTES = F * R * LP * CB;
+  static constexpr int GIN_BYTES = NPL * H * R * CB;
+  static constexpr int KS_BYTES = KIND == ROW_STEP ? R * N * (int)sizeof(T) : 0;
+  static constexpr int RED_BYTES = KIND == ROW_INV_DIAG ? kDiagQ * 1024 * 8 : 0;
+  static constexpr bool STAGE_K = KS_BYTES > 0 && TW_BYTES + BUF_BYTES + KS_BYTES + RED_BYTES <= kSmemLimit;
+  static constexpr bool STAGE_G = GIN_BYTES > 0 &&
+      TW_BYTES + BUF_BYTES + GIN_BYTES + (STAGE_K ? KS_BYTES : 0) + RED_BYTES <= kSmemLimit;
+  static constexpr int OFF_BUF = TW_BYTES;
+  static constexpr int OFF_GIN = OFF_BUF + BUF_BYTES;
+  static constexpr int OFF_KS = OFF_GIN + (STAGE_G ? GIN_BYTES : 0);
+  static constexpr int OFF_RED = OFF_KS + (STAGE_K ? KS_BYTES : 0);
+  static constexpr int SMEM = OFF_RED + RED_BYTES;
+  static constexpr int NT = cmax(64, cmin(1024, F * R * TT));
+  static constexpr int SEG = R * CB;                        // bytes per (plane, mx) segment
+  static constexpr int CHUNK = SEG % 16 == 0 ? 16 : 8;
+  static_assert(SMEM <= 227 * 1024, "row pass does not fit in shared memory");
+  static_assert(N % R == 0, "rows per block must divide N");
 };
 
-// Column-pass geometry: FB transforms in flight, NT threads.
-template <typename T, int N, int MODE>
-struct ColCfg {
-  static constexpr int M = N / 4;
-  static constexpr int H = M + 1;
-  static constexpr int NK = 2 * M + 1;
-  static constexpr int PE = cmin(points_per_thread<T>(), N);
+// Column-pass geometry and shared-memory plan.
+template <typename T, int N, int MODE, int PEV>
+struct ColGeo {
+  static constexpr int M = N / 4, H = M + 1, NK = 2 * M + 1;
+  static constexpr int PE = cmin(PEV, N);
   static constexpr int PS = ilog2(PE);
   static constexpr int LP = padded_len<N, PS>();
   static constexpr int TT = N / PE;
-  static constexpr int FB0 = MODE == COL_MASK ? 1 : 4;
-  static constexpr int FB = (FB0 * LP * (int)sizeof(cplx<T>) <= 160 * 1024) ? FB0
-                          : (2 * LP * (int)sizeof(cplx<T>) <= 160 * 1024 && FB0 >= 2) ? 2 : 1;
+  static constexpr int NF = MODE == COL_STEP ? 3 : MODE == COL_PROJECT ? 2 : MODE == COL_MASK ? 1 : 0;
+  static constexpr int NI = MODE == COL_MASK ? 1 : 4;
+  static constexpr int CB = (int)sizeof(cplx<T>);
+  static constexpr int TW_BYTES = align16(TwTab<T, N>::ENTRIES * CB);
+  static constexpr int ACC_BYTES = align16(NK * CB);
+  static constexpr int WS_BYTES = MODE == COL_STEP ? align16(NK * CB) : 0;
+  static constexpr int FIXED = TW_BYTES + ACC_BYTES + WS_BYTES + 64;
+  static constexpr int FB0 = cmax(NF, NI) >= 4 ? 4 : cmax(NF, NI);
+  static constexpr int FB = (FIXED + FB0 * LP * CB <= kSmemLimit) ? FB0
+                          : (FIXED + 2 * LP * CB <= kSmemLimit && FB0 >= 2) ? 2 : 1;
+  static constexpr int OFF_BUF = TW_BYTES;
+  static constexpr int OFF_ACC = OFF_BUF + FB * LP * CB;
+  static constexpr int OFF_WS = OFF_ACC + ACC_BYTES;
+  static constexpr int OFF_S0 = OFF_WS + WS_BYTES;
+  static constexpr int SMEM = OFF_S0 + 64;
   static constexpr int NT = cmax(64, cmin(1024, FB * TT));
-  static constexpr int SMEM = FB * LP * (int)sizeof(cplx<T>) + NK * (int)sizeof(cplx<T>) + 64;
+  static_assert(SMEM <= 227 * 1024, "column pass does not fit in shared memory");
 };
 
-template <typename T>
-__device__ __forceinline__ bool finite_t(T v) { return isfinite(v); }
-
 // ---------------------------------------------------------------------------------------
-// Row kernels
+// Row pass body (one block = rows [y0, y0 + R))
 // ---------------------------------------------------------------------------------------
-template <typename T, int N, int KIND>
-__global__ void __launch_bounds__(RowCfg<T, N, KIND>::NT)
-row_kernel(Args<T> A) {
-  using Cfg = RowCfg<T, N, KIND>;
-  constexpr int L = Cfg::L, M = N / 4, H = M + 1;
-  constexpr int R = Cfg::R, NT = Cfg::NT, PE = Cfg::PE, PS = Cfg::PS, LP = Cfg::LP;
-  constexpr int FI = row_inv_fields<KIND>();
-  constexpr int FF = row_fwd_fields<KIND>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
-  const int y0 = blockIdx.x * R;
+template <typename T, int N, int KIND, int R, int PEV>
+__device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned char* smem_raw) {
+  using Geo = RowGeo<T, N, KIND, R, PEV>;
+  constexpr int L = Geo::L, M = Geo::M, H = Geo::H;
+  constexpr int NT = Geo::NT, PE = Geo::PE, PS = Geo::PS, LP = Geo::LP;
+  constexpr int FI = Geo::FI, FF = Geo::FF;
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_BUF);
+  cplx<T>* gin = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_GIN);
+  T* ks = reinterpret_cast<T*>(smem_raw + Geo::OFF_KS);
+  const int y0 = blk * R;
   const int tid = threadIdx.x;
-  const cplx<T>* __restrict__ tw = A.tw;
+
+  // ---- stage: twiddles, the G tile (R consecutive y of every stored column), the K rows ----
+  const TwTab<T, N> tw = TwTab<T, N>::fill(reinterpret_cast<cplx<T>*>(smem_raw), A.tw, tid, NT);
+  if constexpr (Geo::STAGE_G) {
+    constexpr int CPS = Geo::SEG / Geo::CHUNK;   // chunks per segment
+    constexpr int PLANE0 = (KIND == ROW_INV_MASK) ? 0 : 0;
+    for (int i = tid; i < Geo::NPL * H * CPS; i += NT) {
+      const int c = i % CPS;
+      const int t = i / CPS;                     // t = pl * H + kx
+      const char* src = reinterpret_cast<const char*>(A.G + ((size_t)(PLANE0 * H + t)) * N + y0) + c * Geo::CHUNK;
+      cp_async<Geo::CHUNK>(reinterpret_cast<char*>(gin + (size_t)t * R) + c * Geo::CHUNK, src);
+    }
+  }
+  if constexpr (Geo::STAGE_K) {
+    constexpr int NCH = R * N * (int)sizeof(T) / 16;
+    const char* src = reinterpret_cast<const char*>(A.K + (size_t)y0 * N);
+    for (int i = tid; i < NCH; i += NT) cp_async16(reinterpret_cast<char*>(ks) + 16 * i, src + 16 * i);
+  }
+  if constexpr (Geo::STAGE_G || Geo::STAGE_K) cp_async_wait_all();
+  __syncthreads();
 
   // ---- inverse row transforms (C2R through an L-point complex transform) ----
   if constexpr (FI > 0) {
@@ -140,17 +187,23 @@ row_kernel(Args<T> A) {
       } else {
         plane = f == 0 ? 0 : f + 1;                 // w, vx, vy
       }
-      const cplx<T>* src = A.G + (size_t)plane * H * N + (y0 + r);
       cplx<T> X = mk<T>(0, 0), Xm = mk<T>(0, 0);
-      if (k <= M) X = src[(size_t)k * N];
       const int km = L - k;
-      if (km <= M) Xm = src[(size_t)km * N];
+      if constexpr (Geo::STAGE_G) {
+        const cplx<T>* src = gin + (size_t)plane * H * R + r;
+        if (k <= M) X = src[k * R];
+        if (km <= M) Xm = src[km * R];
+      } else {
+        const cplx<T>* src = A.G + (size_t)plane * H * N + (y0 + r);
+        if (k <= M) X = src[(size_t)k * N];
+        if (km <= M) Xm = src[(size_t)km * N];
+      }
       if (dx_mul) {
         X = mul_i(X) * (A.dk * (T)k);
         Xm = mul_i(Xm) * (A.dk * (T)km);
       }
       if (k == 0) X.y = 0;   // the mx = 0 entry of a real row is real
-      const cplx<T> w = conjg(tw[k]);          // conj(W_N^k)
+      const cplx<T> w = conjg(tw.get(k));        // conj(W_N^k)
       const cplx<T> s = X + conjg(Xm);
       const cplx<T> d = X - conjg(Xm);
       sm[(f * R + r) * LP + padi<PS>(k)] = s + mul_i(cmul(w, d));
@@ -170,7 +223,9 @@ row_kernel(Args<T> A) {
       const int r = e / N, x = e % N;
       const T w = rl(0, r, x), wx = rl(1, r, x), wy = rl(2, r, x);
       const T vx = rl(3, r, x), vy = rl(4, r, x);
-      const T Kv = A.K[(size_t)(y0 + r) * N + x];
+      T Kv;
+      if constexpr (Geo::STAGE_K) Kv = ks[e];
+      else Kv = A.K[(size_t)(y0 + r) * N + x];
       const T v2 = vx * vx + vy * vy;
       const T c1 = -A.b * v2 - A.gv * Kv;               // line 1
       rl(0, r, x) = c1 * vx;
@@ -178,7 +233,6 @@ row_kernel(Args<T> A) {
       rl(2, r, x) = -A.lam * (vx * wx + vy * wy) - A.gw * Kv * w;   // line 2
     }
   } else if constexpr (KIND == ROW_FWD_VEL || KIND == ROW_FWD_MASK) {
-    __syncthreads();
     for (int e = tid; e < FF * R * N; e += NT) {
       const int x = e % N;
       const int t = e / N;
@@ -215,8 +269,7 @@ row_kernel(Args<T> A) {
       acc[4] += (isfinite(w) && isfinite(vx) && isfinite(vy)) ? 0.0 : 1.0;
     }
     // fixed-order block reduction (deterministic)
-    __syncthreads();
-    double* red = reinterpret_cast<double*>(smem_raw + Cfg::bytes_per_row * R);
+    double* red = reinterpret_cast<double*>(smem_raw + Geo::OFF_RED);
     for (int q = 0; q < kDiagQ; ++q) red[q * 1024 + tid] = acc[q];
     __syncthreads();
     for (int s = 512; s >= 1; s >>= 1) {
@@ -224,7 +277,7 @@ row_kernel(Args<T> A) {
         for (int q = 0; q < kDiagQ; ++q) red[q * 1024 + tid] += red[q * 1024 + tid + s];
       __syncthreads();
     }
-    if (tid < kDiagQ) A.part[(size_t)blockIdx.x * kDiagQ + tid] = red[tid * 1024];
+    if (tid < kDiagQ) A.part[(size_t)blk * kDiagQ + tid] = red[tid * 1024];
   }
 
   // ---- forward row transforms (R2C), keep mx <= N/4 ----
@@ -241,42 +294,49 @@ row_kernel(Args<T> A) {
       const cplx<T> s = Zk + Zm;
       const cplx<T> d = Zk - Zm;
       // X[k] = (Zk + Zm)/2 - (i/2) W^k (Zk - Zm)
-      const cplx<T> X = (s - mul_i(cmul(tw[k], d))) * (T)0.5;
+      const cplx<T> X = (s - mul_i(cmul(tw.get(k), d))) * (T)0.5;
       A.Rr[((size_t)f * H + k) * N + (y0 + r)] = X;
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// Column kernel
+// Column pass body (one block = stored column mx = kx)
 // ---------------------------------------------------------------------------------------
-template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(ColCfg<T, N, MODE>::NT)
-col_kernel(Args<T> A) {
-  using Cfg = ColCfg<T, N, MODE>;
-  constexpr int M = N / 4, H = M + 1, NK = 2 * M + 1;
-  constexpr int PE = Cfg::PE, PS = Cfg::PS, LP = Cfg::LP, NT = Cfg::NT, FB = Cfg::FB;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* acc = buf + FB * LP;
-  T* s0 = reinterpret_cast<T*>(acc + NK);   // [0..1]: k = 0 forward values, [2..3]: v^(0)
-  const int kx = blockIdx.x;
+template <typename T, int N, int MODE, int PEV>
+__device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char* smem_raw) {
+  using Geo = ColGeo<T, N, MODE, PEV>;
+  constexpr int M = Geo::M, H = Geo::H, NK = Geo::NK;
+  constexpr int PE = Geo::PE, PS = Geo::PS, LP = Geo::LP, NT = Geo::NT, FB = Geo::FB;
+  cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_BUF);
+  cplx<T>* acc = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_ACC);
+  cplx<T>* ws = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_WS);
+  T* s0 = reinterpret_cast<T*>(smem_raw + Geo::OFF_S0);   // [0..1]: k = 0 forward values, [2..3]: v^(0)
   const int tid = threadIdx.x;
   const T kxp = A.dk * (T)kx;
   const T invN = (T)1 / (T)N;
-  const cplx<T>* __restrict__ tw = A.tw;
+  constexpr int CB = Geo::CB;
 
+  const TwTab<T, N> tw = TwTab<T, N>::fill(reinterpret_cast<cplx<T>*>(smem_raw), A.tw, tid, NT);
   auto ky_of = [](int j) { return j <= M ? j : j - NK; };
+  // async copy of nb contiguous columns of Rr (fields f0..f0+nb-1) into the padded buffers
+  auto stage_columns = [&](int f0, int nb) {
+    for (int e = tid; e < nb * N; e += NT) {
+      const int b = e / N, y = e % N;
+      cp_async<CB>(buf + b * LP + padi<PS>(y), A.Rr + ((size_t)(f0 + b) * H + kx) * N + y);
+    }
+  };
 
   // ---- forward column transforms and curl assembly ----
   if constexpr (MODE != COL_PROLOGUE) {
-    constexpr int NF = MODE == COL_STEP ? 3 : MODE == COL_PROJECT ? 2 : 1;
+    constexpr int NF = Geo::NF;
+    if constexpr (MODE == COL_STEP) {
+      for (int j = tid; j < NK; j += NT) cp_async<CB>(ws + j, A.what + (size_t)kx * NK + j);
+    }
     for (int f0 = 0; f0 < NF; f0 += FB) {
       const int nb = cmin(FB, NF - f0);
-      for (int e = tid; e < nb * N; e += NT) {
-        const int b = e / N, y = e % N;
-        buf[b * LP + padi<PS>(y)] = A.Rr[((size_t)(f0 + b) * H + kx) * N + y];
-      }
+      stage_columns(f0, nb);
+      cp_async_wait_all();
       fft_batch<T, N, PE, -1, NT, N>(buf, nb, tw);
       for (int j = tid; j < NK; j += NT) {
         const int ky = ky_of(j);
@@ -310,7 +370,7 @@ col_kernel(Args<T> A) {
         const T k2 = A.dk * A.dk * (T)m2;
         const T om = (T)1 - k2;
         const T E = exp((A.a - om * om) * A.dt);
-        const cplx<T> w = A.what[(size_t)kx * NK + j];
+        const cplx<T> w = ws[j];
         const cplx<T> r = acc[j] * invN;
         wn = (w + r * A.dt) * E;
         if (m2 == 0 || m2 > M * M) wn = mk<T>(0, 0);
@@ -360,7 +420,7 @@ col_kernel(Args<T> A) {
   }
 
   // ---- inverse column transforms of the fields the next row pass reads ----
-  constexpr int NI = MODE == COL_MASK ? 1 : 4;
+  constexpr int NI = Geo::NI;
   for (int f0 = 0; f0 < NI; f0 += FB) {
     const int nb = cmin(FB, NI - f0);
     for (int e = tid; e < nb * N; e += NT) {
@@ -393,6 +453,40 @@ col_kernel(Args<T> A) {
     }
     __syncthreads();
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------------------
+template <typename T, int N, int KIND, int R, int PEV>
+__global__ void __launch_bounds__(RowGeo<T, N, KIND, R, PEV>::NT)
+row_kernel(Args<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  row_body<T, N, KIND, R, PEV>(A, blockIdx.x, smem_raw);
+}
+
+template <typename T, int N, int MODE, int PEV>
+__global__ void __launch_bounds__(ColGeo<T, N, MODE, PEV>::NT)
+col_kernel(Args<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  col_body<T, N, MODE, PEV>(A, blockIdx.x, smem_raw);
+}
+
+// Batched variants: blockIdx.y selects the domain, whose arguments live in a device array.
+template <typename T, int N, int KIND, int R, int PEV>
+__global__ void __launch_bounds__(RowGeo<T, N, KIND, R, PEV>::NT)
+row_kernel_batched(const Args<T>* __restrict__ args) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Args<T> A = args[blockIdx.y];
+  row_body<T, N, KIND, R, PEV>(A, blockIdx.x, smem_raw);
+}
+
+template <typename T, int N, int MODE, int PEV>
+__global__ void __launch_bounds__(ColGeo<T, N, MODE, PEV>::NT)
+col_kernel_batched(const Args<T>* __restrict__ args) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const Args<T> A = args[blockIdx.y];
+  col_body<T, N, MODE, PEV>(A, blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -44,23 +44,23 @@ static cudaError_t set_smem(K kernel, int bytes, std::atomic<int>& done) {
   return e;
 }
 
-template <typename T, int N, int KIND>
+template <typename T, int N, int KIND, int R = default_rows<T, N>(), int PE = default_row_pe<T, N>()>
 static cudaError_t launch_row_kind(const DomainDev& d, cudaStream_t s) {
-  using Cfg = RowCfg<T, N, KIND>;
+  using Geo = RowGeo<T, N, KIND, R, PE>;
   static std::atomic<int> done{0};
-  cudaError_t e = set_smem(row_kernel<T, N, KIND>, Cfg::SMEM, done);
+  cudaError_t e = set_smem(row_kernel<T, N, KIND, R, PE>, Geo::SMEM, done);
   if (e != cudaSuccess) return e;
-  row_kernel<T, N, KIND><<<N / Cfg::R, Cfg::NT, Cfg::SMEM, s>>>(make_args<T>(d));
+  row_kernel<T, N, KIND, R, PE><<<N / R, Geo::NT, Geo::SMEM, s>>>(make_args<T>(d));
   return cudaGetLastError();
 }
 
-template <typename T, int N, int MODE>
+template <typename T, int N, int MODE, int PE = default_col_pe<T, N>()>
 static cudaError_t launch_col_mode(const DomainDev& d, cudaStream_t s) {
-  using Cfg = ColCfg<T, N, MODE>;
+  using Geo = ColGeo<T, N, MODE, PE>;
   static std::atomic<int> done{0};
-  cudaError_t e = set_smem(col_kernel<T, N, MODE>, Cfg::SMEM, done);
+  cudaError_t e = set_smem(col_kernel<T, N, MODE, PE>, Geo::SMEM, done);
   if (e != cudaSuccess) return e;
-  col_kernel<T, N, MODE><<<Cfg::H, Cfg::NT, Cfg::SMEM, s>>>(make_args<T>(d));
+  col_kernel<T, N, MODE, PE><<<Geo::H, Geo::NT, Geo::SMEM, s>>>(make_args<T>(d));
   return cudaGetLastError();
 }
 
@@ -79,15 +79,8 @@ static cudaError_t launch_row(int kind, const DomainDev& d, cudaStream_t s) {
 
 template <typename T, int N>
 static int row_blocks(int kind) {
-  switch (kind) {
-    case K_ROW_STEP: return N / RowCfg<T, N, ROW_STEP>::R;
-    case K_ROW_FWD_VEL: return N / RowCfg<T, N, ROW_FWD_VEL>::R;
-    case K_ROW_FWD_MASK: return N / RowCfg<T, N, ROW_FWD_MASK>::R;
-    case K_ROW_INV_FIELDS: return N / RowCfg<T, N, ROW_INV_FIELDS>::R;
-    case K_ROW_INV_MASK: return N / RowCfg<T, N, ROW_INV_MASK>::R;
-    case K_ROW_INV_DIAG: return N / RowCfg<T, N, ROW_INV_DIAG>::R;
-  }
-  return 0;
+  (void)kind;
+  return N / default_rows<T, N>();
 }
 
 template <typename T, int N>

@@ -88,5 +88,6 @@ WORKLOADS = {
     "circle64_fp64": dict(n=64, dx=0.25, radius=5.2, seed=1, steps=2000),
     "circle512": dict(n=512, dx=0.04, radius=5.4, seed=2, steps=20000),
     "circle2048_turbulent": dict(n=2048, dx=0.02, radius=12.0, seed=4, steps=10000),
+    "circle4096_turbulent": dict(n=4096, dx=0.01, radius=12.0, seed=4, steps=1000),
     "circle8192_paper_grid": dict(n=8192, dx=0.005, radius=12.0, seed=4, steps=100),
 }
