@@ -219,6 +219,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- float32 (headline) ----
     dom = ttsh.Domain(mask, n, dx, precision=32, stream=stream.cuda_stream)
     dom.set_velocity(vx0, vy0)
+    plan32 = dom.autotune(iters=max(20, min(400, int(4e7 // (n * n)))))   # untimed
     for _ in range(W):
         dom.step(S)
     dom.synchronize()
@@ -245,6 +246,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_fp64:
         d64 = ttsh.Domain(mask, n, dx, precision=64, stream=stream.cuda_stream)
         d64.set_velocity(vx0, vy0)
+        plan64 = d64.autotune(iters=max(10, min(100, int(1e7 // (n * n)))))
         S64 = max(1, S // 4)
         d64.step(S64)
         d64.synchronize()
@@ -255,7 +257,7 @@ def run_ours(args, rank, world, local_rank):
         v64 = world * n * n * S64 * K / t64
         fp64 = {"value": v64, "unit": UNIT, "solver_steps_per_step": S64,
                 "ms_per_solver_step": 1e3 * t64 / (S64 * K), "row_pass_ms": r64, "col_pass_ms": c64,
-                "fp32_over_fp64": value / v64}
+                "fp32_over_fp64": value / v64, "plan": plan64}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -265,6 +267,7 @@ def run_ours(args, rank, world, local_rank):
         hx[:], hy[:] = vx0, vy0
         ox, oy, ow = pin((n, n)), pin((n, n)), pin((n, n))
         de = ttsh.Domain(mask, n, dx, precision=32, stream=stream.cuda_stream)
+        de.set_plan(plan32["row_variant"], plan32["col_variant"])
         lib = ttsh.load_library()
         P = lambda a: a.ctypes.data_as(ttsh._D)
 
@@ -314,7 +317,7 @@ def run_ours(args, rank, world, local_rank):
         "ms_per_step": 1e3 * t32 / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_desc(args.workload, w, S), "n": n, "dx": dx,
-                   "radius": w["radius"], "solver_steps_per_step": S,
+                   "radius": w["radius"], "solver_steps_per_step": S, "plan": plan32,
                    "l2": "flushed (256 MiB write) before every timed step; the state stays L2-resident within a step",
                    "parallelism": "replicas" if world == 1 else f"independent domains x{world}"},
         "e2e": e2e, "gpu_launches": 2 * S * K, "clocks": clk, "roofline": roofline,

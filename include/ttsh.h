@@ -146,13 +146,26 @@ ttsh_status ttsh_set_spectral_state(ttsh_domain* d, const double* w_hat, const d
 ttsh_status ttsh_diagnostics(ttsh_domain* d, ttsh_diag* out, double* spectrum, int32_t nbins,
                              const double* centre);
 
-/* Kernel timing for roofline reports: launches the row pass `iters` times back to back and
- * then the column pass `iters` times, each run bracketed by CUDA events on the domain's
- * stream, and writes the mean duration of one launch in milliseconds to ms[0] (row pass)
- * and ms[1] (column pass).  The spectral state and inter-pass buffers are saved before and
+/* Kernel timing for roofline reports: records `iters` back-to-back launches of the row pass
+ * (then of the column pass) of the current plan as CUDA graphs, replays them between CUDA
+ * events on the domain's stream and writes the mean duration of one launch in milliseconds
+ * to ms[0] (row pass) and ms[1] (column pass).  The spectral state is saved before and
  * restored after, so the domain continues exactly where it was.  Synchronises.
  * iters must be in [1, 1000000]. */
 ttsh_status ttsh_time_kernels(ttsh_domain* d, int32_t iters, double* ms);
+
+/* Step-kernel tile shapes ("plan").  Each grid size has a list of row-pass variants (rows
+ * per block, points per thread of the register butterflies) and column-pass variants
+ * (points per thread); entry 0 is the default.  Variants compute the same step with a
+ * different factorisation of the transforms, so results agree to rounding, not bit for bit.
+ * ttsh_autotune times every variant (as ttsh_time_kernels does, `iters` launches each, state
+ * restored) and selects the fastest row and column variant.  plan (8 int32, may be NULL):
+ * {row variant, column variant, rows per block, row points per thread, column points per
+ * thread, number of row variants, number of column variants, 0}.  ttsh_set_plan selects
+ * variants by index (TTSH_E_INVALID if out of range). */
+ttsh_status ttsh_autotune(ttsh_domain* d, int32_t iters, int32_t* plan);
+ttsh_status ttsh_get_plan(ttsh_domain* d, int32_t* plan);
+ttsh_status ttsh_set_plan(ttsh_domain* d, int32_t row_variant, int32_t col_variant);
 
 /* Advance a caller-owned state by nsteps steps of Algorithm 1 without allocating any device
  * memory (the paper has no counterpart: this is a library convenience).  It is meant for

@@ -120,6 +120,7 @@ struct ttsh_domain {
   int64_t steps;
   cudaGraphExec_t graph;
   int graph_len;
+  int rv, cv;   // selected tile shapes of the row and column step kernels
 };
 
 namespace {
@@ -139,9 +140,69 @@ ttsh_status run_col(ttsh_domain* d, int mode, cudaStream_t s) {
 }
 
 ttsh_status one_step(ttsh_domain* d, cudaStream_t s) {
-  ttsh_status st = run_row(d, ttsh::K_ROW_STEP, s);
+  cudaError_t e = d->ops.row_step[d->rv].fn(d->dev, s);
+  if (e != cudaSuccess) return cuda_fail(e, "row pass launch");
+  e = d->ops.col_step[d->cv].fn(d->dev, s);
+  if (e != cudaSuccess) return cuda_fail(e, "column pass launch");
+  return TTSH_OK;
+}
+
+// Mean duration of one launch of fn, from CUDA events around graph replays (the launches are
+// recorded in graphs of up to 128 so that host launch overhead is not timed).
+ttsh_status time_launches(ttsh_domain* d, ttsh::StepFn fn, int iters, double* ms) {
+  cudaError_t e = fn(d->dev, d->stream);   // sets kernel attributes outside capture
+  if (e != cudaSuccess) return cuda_fail(e, "timing warm-up");
+  const int per = iters < 128 ? iters : 128;
+  const int reps = (iters + per - 1) / per;
+  TTSH_CUDA(cudaStreamSynchronize(d->stream), "timing warm-up");
+  TTSH_CUDA(cudaStreamBeginCapture(d->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+  for (int i = 0; i < per && e == cudaSuccess; ++i) e = fn(d->dev, d->capture);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(d->capture, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(e != cudaSuccess ? e : e2, "timing capture");
+  }
+  cudaGraphExec_t ge = nullptr;
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "timing graph instantiate");
+  cudaEvent_t ev[2];
+  cudaEventCreate(&ev[0]);
+  cudaEventCreate(&ev[1]);
+  e = cudaGraphLaunch(ge, d->stream);   // warm
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], d->stream);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(ge, d->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], d->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  cudaGraphExecDestroy(ge);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel timing");
+  *ms = (double)t / ((double)reps * per);
+  return TTSH_OK;
+}
+
+// Save / restore the spectral state around timing runs of the column pass.
+ttsh_status save_state(ttsh_domain* d) {
+  const size_t wbytes = (size_t)d->H * d->NK * 2 * d->elt;
+  char* save = static_cast<char*>(d->ws) + d->lay.save;
+  TTSH_CUDA(cudaMemcpyAsync(save, d->dev.what, wbytes, cudaMemcpyDeviceToDevice, d->stream), "save state");
+  TTSH_CUDA(cudaMemcpyAsync(save + wbytes, d->dev.vmean, 64, cudaMemcpyDeviceToDevice, d->stream), "save mean");
+  return TTSH_OK;
+}
+
+ttsh_status restore_state(ttsh_domain* d) {
+  const size_t wbytes = (size_t)d->H * d->NK * 2 * d->elt;
+  char* save = static_cast<char*>(d->ws) + d->lay.save;
+  TTSH_CUDA(cudaMemcpyAsync(d->dev.what, save, wbytes, cudaMemcpyDeviceToDevice, d->stream), "restore state");
+  TTSH_CUDA(cudaMemcpyAsync(d->dev.vmean, save + wbytes, 64, cudaMemcpyDeviceToDevice, d->stream), "restore mean");
+  ttsh_status st = run_col(d, ttsh::K_COL_PROLOGUE, d->stream);
   if (st != TTSH_OK) return st;
-  return run_col(d, ttsh::K_COL_STEP, s);
+  TTSH_CUDA(cudaStreamSynchronize(d->stream), "restore state");
+  return TTSH_OK;
 }
 
 ttsh_status sync(ttsh_domain* d, const char* what) {
@@ -278,6 +339,8 @@ ttsh_status ttsh_create_domain(const uint8_t* mask, const ttsh_params* p, void* 
   d->steps = 0;
   d->graph = nullptr;
   d->graph_len = 0;
+  d->rv = 0;
+  d->cv = 0;
   d->lay = layout_for(d->n, d->elt);
   d->owns_ws = workspace == nullptr;
   d->ws = workspace;
@@ -537,34 +600,65 @@ ttsh_status ttsh_diagnostics(ttsh_domain* d, ttsh_diag* out, double* spectrum, i
 ttsh_status ttsh_time_kernels(ttsh_domain* d, int32_t iters, double* ms) {
   if (!d || !ms) return fail(TTSH_E_INVALID, "NULL argument");
   if (iters < 1 || iters > 1000000) return fail(TTSH_E_INVALID, "iters must be in [1, 1000000]");
-  cudaStream_t s = d->stream;
-  const size_t wbytes = (size_t)d->H * d->NK * 2 * d->elt;
-  char* save = static_cast<char*>(d->ws) + d->lay.save;
-  TTSH_CUDA(cudaMemcpyAsync(save, d->dev.what, wbytes, cudaMemcpyDeviceToDevice, s), "save state");
-  TTSH_CUDA(cudaMemcpyAsync(save + wbytes, d->dev.vmean, 64, cudaMemcpyDeviceToDevice, s), "save mean");
-  cudaEvent_t ev[4];
-  for (int i = 0; i < 4; ++i) TTSH_CUDA(cudaEventCreate(&ev[i]), "event create");
-  ttsh_status st = TTSH_OK;
-  cudaEventRecord(ev[0], s);
-  for (int i = 0; i < iters && st == TTSH_OK; ++i) st = run_row(d, ttsh::K_ROW_STEP, s);
-  cudaEventRecord(ev[1], s);
-  cudaEventRecord(ev[2], s);
-  for (int i = 0; i < iters && st == TTSH_OK; ++i) st = run_col(d, ttsh::K_COL_STEP, s);
-  cudaEventRecord(ev[3], s);
-  cudaError_t e = cudaStreamSynchronize(s);
-  float t0 = 0.f, t1 = 0.f;
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&t0, ev[0], ev[1]);
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[2], ev[3]);
-  for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+  ttsh_status st = save_state(d);
   if (st != TTSH_OK) return st;
-  if (e != cudaSuccess) return cuda_fail(e, "kernel timing");
-  ms[0] = t0 / iters;
-  ms[1] = t1 / iters;
-  // restore the state and rebuild the inverse-transformed fields from it
-  TTSH_CUDA(cudaMemcpyAsync(d->dev.what, save, wbytes, cudaMemcpyDeviceToDevice, s), "restore state");
-  TTSH_CUDA(cudaMemcpyAsync(d->dev.vmean, save + wbytes, 64, cudaMemcpyDeviceToDevice, s), "restore mean");
-  if ((st = run_col(d, ttsh::K_COL_PROLOGUE, s)) != TTSH_OK) return st;
-  return sync(d, "time_kernels");
+  if ((st = time_launches(d, d->ops.row_step[d->rv].fn, iters, &ms[0])) != TTSH_OK) return st;
+  if ((st = time_launches(d, d->ops.col_step[d->cv].fn, iters, &ms[1])) != TTSH_OK) return st;
+  return restore_state(d);
+}
+
+ttsh_status ttsh_autotune(ttsh_domain* d, int32_t iters, int32_t* plan) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  if (iters < 1 || iters > 100000) return fail(TTSH_E_INVALID, "iters must be in [1, 100000]");
+  ttsh_status st = save_state(d);
+  if (st != TTSH_OK) return st;
+  double best = 1e300;
+  int br = 0, bc = 0;
+  for (int i = 0; i < d->ops.n_row_variants; ++i) {
+    double t;
+    if ((st = time_launches(d, d->ops.row_step[i].fn, iters, &t)) != TTSH_OK) return st;
+    if (t < best) { best = t; br = i; }
+  }
+  best = 1e300;
+  for (int i = 0; i < d->ops.n_col_variants; ++i) {
+    double t;
+    if ((st = time_launches(d, d->ops.col_step[i].fn, iters, &t)) != TTSH_OK) return st;
+    if (t < best) { best = t; bc = i; }
+  }
+  if ((st = restore_state(d)) != TTSH_OK) return st;
+  return ttsh_set_plan(d, br, bc) == TTSH_OK ? ttsh_get_plan(d, plan) : TTSH_E_INVALID;
+}
+
+ttsh_status ttsh_get_plan(ttsh_domain* d, int32_t* plan) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  if (plan) {
+    plan[0] = d->rv;
+    plan[1] = d->cv;
+    plan[2] = d->ops.row_step[d->rv].rows;
+    plan[3] = d->ops.row_step[d->rv].pe;
+    plan[4] = d->ops.col_step[d->cv].pe;
+    plan[5] = d->ops.n_row_variants;
+    plan[6] = d->ops.n_col_variants;
+    plan[7] = 0;
+  }
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_set_plan(ttsh_domain* d, int32_t row_variant, int32_t col_variant) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  if (row_variant < 0 || row_variant >= d->ops.n_row_variants || col_variant < 0 ||
+      col_variant >= d->ops.n_col_variants)
+    return fail(TTSH_E_INVALID, "variant index out of range");
+  if (row_variant != d->rv || col_variant != d->cv) {
+    if (d->graph) {
+      cudaGraphExecDestroy(d->graph);
+      d->graph = nullptr;
+      d->graph_len = 0;
+    }
+    d->rv = row_variant;
+    d->cv = col_variant;
+  }
+  return TTSH_OK;
 }
 
 ttsh_status ttsh_synchronize(ttsh_domain* d) {

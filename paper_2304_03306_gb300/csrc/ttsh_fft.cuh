@@ -13,9 +13,9 @@
 // memory is padded by one slot every PE elements so that the stride-PE writes of the first
 // stage hit distinct banks.
 //
-// Twiddles W_N^m = exp(-2 pi i m / N) come from two small shared-memory tables,
-// W_N^m = W_N^{(m >> S) 2^S} * W_N^{m mod 2^S} with 2^S ~ sqrt(N), filled once per block from
-// a correctly rounded global table; no stage waits on global memory.
+// Twiddles W_N^m = exp(-2 pi i m / N) come from shared memory (the whole table when it fits
+// in 16 KB, else two tables of ~sqrt(N) entries whose product gives W_N^m), filled once per
+// block from a correctly rounded global table; no stage waits on global memory.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -110,11 +110,13 @@ __device__ __forceinline__ void dft_reg(cplx<T>* v) {
   }
 }
 
-// Two-level twiddle table in shared memory for W_TWN^m, m in [0, TWN).
+// Twiddle table in shared memory for W_TWN^m, m in [0, TWN): the full table when it takes at
+// most 16 KB, otherwise two levels W^m = W^{(m >> S) 2^S} * W^{m mod 2^S}.
 template <typename T, int TWN>
 struct TwTab {
+  static constexpr bool FULL = TWN * (int)sizeof(cplx<T>) <= 16384;
   static constexpr int LOG = ilog2(TWN);
-  static constexpr int SB = (LOG + 1) / 2;
+  static constexpr int SB = FULL ? LOG : (LOG + 1) / 2;
   static constexpr int NLO = 1 << SB;
   static constexpr int NHI = TWN >> SB;
   static constexpr int ENTRIES = NLO + NHI;

@@ -103,8 +103,7 @@ struct RowGeo {
   static constexpr int NT = cmax(64, cmin(1024, F * R * TT));
   static constexpr int SEG = R * CB;                        // bytes per (plane, mx) segment
   static constexpr int CHUNK = SEG % 16 == 0 ? 16 : 8;
-  static_assert(SMEM <= 227 * 1024, "row pass does not fit in shared memory");
-  static_assert(N % R == 0, "rows per block must divide N");
+  static constexpr bool VALID = SMEM <= 227 * 1024 && N % R == 0 && R <= N && TT <= 1024 && NT % TT == 0;
 };
 
 // Column-pass geometry and shared-memory plan.
@@ -131,7 +130,7 @@ struct ColGeo {
   static constexpr int OFF_S0 = OFF_WS + WS_BYTES;
   static constexpr int SMEM = OFF_S0 + 64;
   static constexpr int NT = cmax(64, cmin(1024, FB * TT));
-  static_assert(SMEM <= 227 * 1024, "column pass does not fit in shared memory");
+  static constexpr bool VALID = SMEM <= 227 * 1024 && TT <= 1024 && NT % TT == 0;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -140,6 +139,7 @@ struct ColGeo {
 template <typename T, int N, int KIND, int R, int PEV>
 __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned char* smem_raw) {
   using Geo = RowGeo<T, N, KIND, R, PEV>;
+  static_assert(Geo::VALID, "row pass tile does not fit");
   constexpr int L = Geo::L, M = Geo::M, H = Geo::H;
   constexpr int NT = Geo::NT, PE = Geo::PE, PS = Geo::PS, LP = Geo::LP;
   constexpr int FI = Geo::FI, FF = Geo::FF;
@@ -306,6 +306,7 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
 template <typename T, int N, int MODE, int PEV>
 __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char* smem_raw) {
   using Geo = ColGeo<T, N, MODE, PEV>;
+  static_assert(Geo::VALID, "column pass tile does not fit");
   constexpr int M = Geo::M, H = Geo::H, NK = Geo::NK;
   constexpr int PE = Geo::PE, PS = Geo::PS, LP = Geo::LP, NT = Geo::NT, FB = Geo::FB;
   cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_BUF);

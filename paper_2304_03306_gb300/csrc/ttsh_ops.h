@@ -34,11 +34,26 @@ using ColFn = cudaError_t (*)(int mode, const DomainDev&, cudaStream_t);
 using SpecFn = cudaError_t (*)(const DomainDev&, int nbins, cudaStream_t);
 using BlocksFn = int (*)(int kind);
 
+using StepFn = cudaError_t (*)(const DomainDev&, cudaStream_t);
+
+// One tile shape of a step kernel: rows per block (row pass only) and points per thread of
+// the register butterflies.
+struct StepVariant {
+  StepFn fn;
+  int rows;
+  int pe;
+};
+
+constexpr int kMaxVariants = 8;
+
 struct SizeOps {
   RowFn row;
   ColFn col;
   SpecFn spec;
   BlocksFn row_blocks;   // grid size of a row kernel kind (number of diagnostic partials)
+  int n_row_variants, n_col_variants;           // entry 0 is the default tile shape
+  StepVariant row_step[kMaxVariants];
+  StepVariant col_step[kMaxVariants];
 };
 
 // Per translation unit registries; return false if the TU does not hold size n.

@@ -101,6 +101,26 @@ static cudaError_t launch_spec(const DomainDev& d, int nbins, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T, int N, int R, int PE>
+static void add_row_variant(SizeOps& o) {
+  if constexpr (RowGeo<T, N, ROW_STEP, R, PE>::VALID && (N >= 64 || (R == default_rows<T, N>() && PE == default_row_pe<T, N>()))) {
+    for (int i = 0; i < o.n_row_variants; ++i)
+      if (o.row_step[i].rows == R && o.row_step[i].pe == cmin(PE, N / 2)) return;   // same shape
+    if (o.n_row_variants < kMaxVariants)
+      o.row_step[o.n_row_variants++] = StepVariant{&launch_row_kind<T, N, ROW_STEP, R, PE>, R, cmin(PE, N / 2)};
+  }
+}
+
+template <typename T, int N, int PE>
+static void add_col_variant(SizeOps& o) {
+  if constexpr (ColGeo<T, N, COL_STEP, PE>::VALID && (N >= 64 || PE == default_col_pe<T, N>())) {
+    for (int i = 0; i < o.n_col_variants; ++i)
+      if (o.col_step[i].pe == cmin(PE, N)) return;
+    if (o.n_col_variants < kMaxVariants)
+      o.col_step[o.n_col_variants++] = StepVariant{&launch_col_mode<T, N, COL_STEP, PE>, 1, cmin(PE, N)};
+  }
+}
+
 template <typename T, int N>
 static SizeOps make_ops() {
   SizeOps o;
@@ -108,6 +128,25 @@ static SizeOps make_ops() {
   o.col = &launch_col<T, N>;
   o.spec = &launch_spec<T, N>;
   o.row_blocks = &row_blocks<T, N>;
+  o.n_row_variants = 0;
+  o.n_col_variants = 0;
+  add_row_variant<T, N, default_rows<T, N>(), default_row_pe<T, N>()>(o);
+  add_col_variant<T, N, default_col_pe<T, N>()>(o);
+  if constexpr (sizeof(T) == 4) {
+    add_row_variant<T, N, 4, 16>(o);
+    add_row_variant<T, N, 2, 16>(o);
+    add_row_variant<T, N, 1, 16>(o);
+    add_row_variant<T, N, 2, 8>(o);
+    add_col_variant<T, N, 8>(o);
+    add_col_variant<T, N, 16>(o);
+    add_col_variant<T, N, 4>(o);
+  } else {
+    add_row_variant<T, N, 2, 8>(o);
+    add_row_variant<T, N, 1, 8>(o);
+    add_row_variant<T, N, 1, 4>(o);
+    add_col_variant<T, N, 8>(o);
+    add_col_variant<T, N, 4>(o);
+  }
   return o;
 }
 

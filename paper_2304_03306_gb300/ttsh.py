@@ -72,6 +72,9 @@ def load_library(path: str = LIB_PATH):
         "ttsh_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(ttsh_diag), _D, ctypes.c_int32, _D]),
         "ttsh_synchronize": (ctypes.c_int, [_P]),
         "ttsh_time_kernels": (ctypes.c_int, [_P, ctypes.c_int32, _D]),
+        "ttsh_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+        "ttsh_get_plan": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+        "ttsh_set_plan": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
         "ttsh_step_count": (ctypes.c_int64, [_P]),
         "ttsh_step_noalloc": (ctypes.c_int, [ctypes.POINTER(ttsh_params), _P, _P, _P, ctypes.c_int64, _P]),
         "ttsh_last_error": (ctypes.c_char_p, []),
@@ -195,6 +198,30 @@ def ttsh_time_kernels(h, iters: int):
     return float(ms[0]), float(ms[1])
 
 
+_PLAN_KEYS = ("row_variant", "col_variant", "rows_per_block", "row_points_per_thread",
+              "col_points_per_thread", "n_row_variants", "n_col_variants")
+
+
+def _plan_dict(buf):
+    return {k: int(buf[i]) for i, k in enumerate(_PLAN_KEYS)}
+
+
+def ttsh_autotune(h, iters: int = 200) -> dict:
+    buf = (ctypes.c_int32 * 8)()
+    _check(load_library().ttsh_autotune(h, int(iters), buf))
+    return _plan_dict(buf)
+
+
+def ttsh_get_plan(h) -> dict:
+    buf = (ctypes.c_int32 * 8)()
+    _check(load_library().ttsh_get_plan(h, buf))
+    return _plan_dict(buf)
+
+
+def ttsh_set_plan(h, row_variant: int, col_variant: int):
+    _check(load_library().ttsh_set_plan(h, int(row_variant), int(col_variant)))
+
+
 def ttsh_synchronize(h):
     _check(load_library().ttsh_synchronize(h))
 
@@ -259,6 +286,16 @@ class Domain:
 
     def synchronize(self):
         ttsh_synchronize(self.h)
+
+    def autotune(self, iters: int = 200) -> dict:
+        """Time every tile-shape variant of the step kernels and keep the fastest."""
+        return ttsh_autotune(self.h, iters)
+
+    def plan(self) -> dict:
+        return ttsh_get_plan(self.h)
+
+    def set_plan(self, row_variant: int, col_variant: int):
+        ttsh_set_plan(self.h, row_variant, col_variant)
 
     def time_kernels(self, iters: int):
         """Mean (row pass, column pass) launch durations in ms, state restored afterwards."""

@@ -286,3 +286,42 @@ def test_rotation_symmetry_on_gpu(T):
     bx, by, bw = b.fields()
     assert rel(np.stack([bx, by]), np.stack([-ay[sy, sx], ax[sy, sx]])) <= 1e-12
     assert rel(bw, aw[sy, sx]) <= 1e-12
+
+
+# ------------------------------------------------------- tile-shape variants / autotuner
+
+@pytest.mark.parametrize("prec,n,dx,R", [(32, 64, 0.25, 5.2), (32, 512, 0.04, 5.4), (64, 128, 0.16, 5.3),
+                                         (32, 2048, 0.02, 12.0)])
+def test_every_step_variant_matches_oracle(T, prec, n, dx, R):
+    steps = 20 if n <= 512 else 2
+    dom, p, K, s = setup(T, n, dx, R, prec, 3, amp=0.3)
+    w0, v00 = dom.spectral_state()
+    ref = O.run(s, K, p, steps)
+    plan = dom.plan()
+    assert plan["n_row_variants"] >= 1 and plan["n_col_variants"] >= 1
+    for rv in range(plan["n_row_variants"]):
+        for cv in range(plan["n_col_variants"]):
+            dom.set_plan(rv, cv)
+            dom.set_spectral_state(w0, v00)
+            dom.step(steps)
+            vx, vy, w = dom.fields()
+            assert rel(w, O.vorticity(ref)) <= TOL[prec], (rv, cv)
+            assert rel(np.stack([vx, vy]), np.stack([ref.vx, ref.vy])) <= TOL[prec], (rv, cv)
+
+
+def test_autotune_selects_a_valid_plan_and_keeps_state(T):
+    n, dx = 256, 0.08
+    dom, p, K, s = setup(T, n, dx, 5.6, 32, 8, amp=0.3)
+    before = dom.spectral_state()
+    plan = dom.autotune(iters=20)
+    after = dom.spectral_state()
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    assert 0 <= plan["row_variant"] < plan["n_row_variants"]
+    assert 0 <= plan["col_variant"] < plan["n_col_variants"]
+    assert plan == dom.plan()
+    dom.step(30)
+    vx, vy, w = dom.fields()
+    ref = O.run(s, K, p, 30)
+    assert rel(w, O.vorticity(ref)) <= TOL[32]
+    with pytest.raises(T.TTSHError):
+        dom.set_plan(plan["n_row_variants"], 0)
