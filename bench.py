@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -259,6 +260,32 @@ def run_ours(args, rank, world, local_rank):
                 "ms_per_solver_step": 1e3 * t64 / (S64 * K), "row_pass_ms": r64, "col_pass_ms": c64,
                 "fp32_over_fp64": value / v64, "plan": plan64}
 
+    # ---- batched sweep: 48 domains (128^2..512^2 circles and dumbbells) in lock step ----
+    batched = None
+    if not args.no_batch:
+        sweep = ti.sweep_domains()
+        objs = []
+        for dspec in sweep:
+            o = ttsh.Domain(dspec["mask"], dspec["n"], dspec["dx"], precision=32, stream=stream.cuda_stream)
+            bvx, bvy = ti.noise_velocity(dspec["mask"], dspec["seed"] + 1000 * rank, 0.01)
+            o.set_velocity(bvx, bvy)
+            objs.append(o)
+        bt = ttsh.Batch(objs, stream=stream.cuda_stream)
+        Sb = max(32, S // 20)
+        bt.step(Sb)
+        bt.synchronize()
+        barrier()
+        tb = max_over_ranks(timed_segments(bt, K, Sb))
+        pts = sum(dspec["n"] ** 2 for dspec in sweep)
+        batched = {"value": world * pts * Sb * K / tb, "unit": UNIT, "domains": len(sweep),
+                   "grid_points": pts, "solver_steps_per_step": Sb, "launch_groups": bt.groups,
+                   "ms_per_solver_step": 1e3 * tb / (Sb * K),
+                   "workload": "24 circles (R 5.0-8.0, forward and backward members) + 24 dumbbells "
+                               "(R in {2.8, pi, 3.5} x D/R 1.0-1.9) on 128^2-512^2 grids, noise 0.01"}
+        bt.close()
+        for o in objs:
+            o.close()
+
     # ---- end to end through the public API with host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -321,7 +348,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed (256 MiB write) before every timed step; the state stays L2-resident within a step",
                    "parallelism": "replicas" if world == 1 else f"independent domains x{world}"},
         "e2e": e2e, "gpu_launches": 2 * S * K, "clocks": clk, "roofline": roofline,
-        "cpu_baseline": cpu, "fp64": fp64,
+        "cpu_baseline": cpu, "fp64": fp64, "batched": batched,
         "diagnostics_after": {"energy": diag["energy"], "psi": diag["psi"], "nonfinite": diag["nonfinite"]},
         "ms_per_solver_step": 1e3 * t32 / (K * S),
     }

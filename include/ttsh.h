@@ -75,6 +75,7 @@ typedef struct {
 } ttsh_diag;
 
 typedef struct ttsh_domain ttsh_domain;
+typedef struct ttsh_batch ttsh_batch;
 
 /* Fill *p with the Table I constants (Appendix B).  Never fails. */
 void ttsh_default_params(ttsh_params* p);
@@ -187,6 +188,24 @@ ttsh_status ttsh_set_plan(ttsh_domain* d, int32_t row_variant, int32_t col_varia
  * waiting for them. */
 ttsh_status ttsh_step_noalloc(const ttsh_params* p, const void* K, void* w_hat, void* v0,
                               int64_t nsteps, void* stream);
+
+/* Batched stepping of many independent domains, as the paper's radius and dumbbell sweeps
+ * (Sec. III.C, Sec. IV) need: dozens of small domains of uneven sizes advanced together.
+ * ttsh_batch_create groups the domains by (precision, n, plan); every group advances in one
+ * launch per pass (row, column) for all its domains, and the groups run as parallel branches
+ * of one CUDA graph replayed 32 steps at a time.  Each domain's result is bit-identical to
+ * ttsh_step on that domain alone.
+ *   domains  ndom distinct handles (ndom >= 1), each with n <= 1024 (TTSH_E_UNSUPPORTED
+ *            otherwise); they must outlive the batch and are not copied.  The plan each
+ *            domain has at creation is used; later ttsh_set_plan calls do not affect it.
+ *   stream   stream the batch is issued on (NULL = legacy default).
+ * ttsh_batch_step advances every domain by nsteps (asynchronous; it first waits for each
+ * domain's own stream to be idle) and adds nsteps to their step counters. */
+ttsh_status ttsh_batch_create(ttsh_domain* const* domains, int32_t ndom, void* stream, ttsh_batch** out);
+ttsh_status ttsh_batch_step(ttsh_batch* b, int64_t nsteps);
+ttsh_status ttsh_batch_synchronize(ttsh_batch* b);
+int32_t ttsh_batch_groups(const ttsh_batch* b);   /* number of launch groups, -1 if NULL */
+void ttsh_batch_destroy(ttsh_batch* b);           /* NULL is a no-op; domains are untouched */
 
 /* Block the host until the domain's stream is idle; reports deferred CUDA errors. */
 ttsh_status ttsh_synchronize(ttsh_domain* d);

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <unordered_set>
 #include <vector>
 
 #include "ttsh.h"
@@ -291,6 +292,76 @@ cudaError_t launch_spectrum_reduce(const double* colhist, int ncols, int nbins, 
 }
 
 }  // namespace ttsh
+
+
+// ---------------------------------------------------------------------------------------
+// Batched stepping: domains grouped by (precision, n, plan); one launch per pass per group
+// advances every domain of the group (blockIdx.y = domain).  Groups are independent, so each
+// runs its own launch chain in a parallel branch of one CUDA graph.
+// ---------------------------------------------------------------------------------------
+struct BatchGroup {
+  int precision = 0, n = 0, rv = 0, cv = 0;
+  std::vector<ttsh_domain*> doms;
+  void* args_dev = nullptr;
+  const ttsh::StepVariant* row = nullptr;
+  const ttsh::StepVariant* col = nullptr;
+  cudaStream_t branch = nullptr;
+  cudaEvent_t join = nullptr;
+};
+
+struct ttsh_batch {
+  std::vector<BatchGroup> groups;
+  std::vector<ttsh_domain*> all;
+  cudaStream_t stream = nullptr;
+  cudaStream_t capture = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+};
+
+namespace {
+
+constexpr int kBatchGraphLen = 32;
+
+ttsh_status batch_group_steps(BatchGroup& g, int nsteps, cudaStream_t s) {
+  const int nd = (int)g.doms.size();
+  for (int i = 0; i < nsteps; ++i) {
+    cudaError_t e = g.row->batched(g.args_dev, nd, s);
+    if (e == cudaSuccess) e = g.col->batched(g.args_dev, nd, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+  }
+  return TTSH_OK;
+}
+
+ttsh_status batch_build_graph(ttsh_batch* b) {
+  TTSH_CUDA(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+  ttsh_status st = TTSH_OK;
+  cudaError_t e = cudaEventRecord(b->fork, b->capture);
+  for (size_t i = 0; i < b->groups.size() && e == cudaSuccess && st == TTSH_OK; ++i) {
+    BatchGroup& g = b->groups[i];
+    e = cudaStreamWaitEvent(g.branch, b->fork, 0);
+    if (e == cudaSuccess) st = batch_group_steps(g, kBatchGraphLen, g.branch);
+    if (e == cudaSuccess && st == TTSH_OK) e = cudaEventRecord(g.join, g.branch);
+    if (e == cudaSuccess && st == TTSH_OK) e = cudaStreamWaitEvent(b->capture, g.join, 0);
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(b->capture, &graph);
+  if (st != TTSH_OK || e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    if (st != TTSH_OK) return st;
+    return cuda_fail(e != cudaSuccess ? e : e2, "batch capture");
+  }
+  e = cudaGraphInstantiate(&b->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    b->graph = nullptr;
+    return cuda_fail(e, "batch graph instantiate");
+  }
+  b->graph_len = kBatchGraphLen;
+  return TTSH_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -659,6 +730,102 @@ ttsh_status ttsh_set_plan(ttsh_domain* d, int32_t row_variant, int32_t col_varia
     d->cv = col_variant;
   }
   return TTSH_OK;
+}
+
+
+ttsh_status ttsh_batch_create(ttsh_domain* const* domains, int32_t ndom, void* stream, ttsh_batch** out) {
+  if (!out) return fail(TTSH_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!domains || ndom < 1) return fail(TTSH_E_INVALID, "need at least one domain");
+  std::unordered_set<ttsh_domain*> seen;
+  for (int i = 0; i < ndom; ++i) {
+    ttsh_domain* d = domains[i];
+    if (!d) return fail(TTSH_E_INVALID, "NULL domain in batch");
+    if (!seen.insert(d).second) return fail(TTSH_E_INVALID, "a domain appears twice in the batch");
+    if (!d->ops.row_step[d->rv].batched || !d->ops.col_step[d->cv].batched)
+      return fail(TTSH_E_UNSUPPORTED, "batched stepping supports n <= 1024");
+  }
+  ttsh_batch* b = new ttsh_batch();
+  b->stream = static_cast<cudaStream_t>(stream);
+  auto cleanup = [&](ttsh_status st) {
+    ttsh_batch_destroy(b);
+    return st;
+  };
+  for (int i = 0; i < ndom; ++i) {
+    ttsh_domain* d = domains[i];
+    b->all.push_back(d);
+    BatchGroup* g = nullptr;
+    for (auto& x : b->groups)
+      if (x.precision == d->p.precision && x.n == d->n && x.rv == d->rv && x.cv == d->cv) g = &x;
+    if (!g) {
+      b->groups.emplace_back();
+      g = &b->groups.back();
+      g->precision = d->p.precision;
+      g->n = d->n;
+      g->rv = d->rv;
+      g->cv = d->cv;
+      g->row = &d->ops.row_step[d->rv];
+      g->col = &d->ops.col_step[d->cv];
+    }
+    g->doms.push_back(d);
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "batch streams"));
+  for (auto& g : b->groups) {
+    const int ab = g.doms[0]->ops.args_bytes;
+    std::vector<unsigned char> host((size_t)ab * g.doms.size());
+    for (size_t k = 0; k < g.doms.size(); ++k) g.doms[k]->ops.pack_args(g.doms[k]->dev, host.data() + k * ab);
+    e = cudaMalloc(&g.args_dev, host.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g.args_dev, host.data(), host.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.branch, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = g.row->prepare();
+    if (e == cudaSuccess) e = g.col->prepare();
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "batch set-up"));
+  }
+  *out = b;
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_batch_step(ttsh_batch* b, int64_t nsteps) {
+  if (!b) return fail(TTSH_E_INVALID, "batch is NULL");
+  if (nsteps < 0) return fail(TTSH_E_INVALID, "nsteps must be >= 0");
+  // every domain's own stream must be idle before the batch writes its state
+  for (ttsh_domain* d : b->all) TTSH_CUDA(cudaStreamSynchronize(d->stream), "domain stream");
+  ttsh_status st;
+  int64_t left = nsteps;
+  if (left >= kBatchGraphLen && !b->graph)
+    if ((st = batch_build_graph(b)) != TTSH_OK) return st;
+  while (b->graph && left >= b->graph_len) {
+    TTSH_CUDA(cudaGraphLaunch(b->graph, b->stream), "batch graph launch");
+    left -= b->graph_len;
+  }
+  for (auto& g : b->groups)
+    if ((st = batch_group_steps(g, (int)left, b->stream)) != TTSH_OK) return st;
+  for (ttsh_domain* d : b->all) d->steps += nsteps;
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_batch_synchronize(ttsh_batch* b) {
+  if (!b) return fail(TTSH_E_INVALID, "batch is NULL");
+  TTSH_CUDA(cudaStreamSynchronize(b->stream), "batch synchronize");
+  return TTSH_OK;
+}
+
+int32_t ttsh_batch_groups(const ttsh_batch* b) { return b ? (int32_t)b->groups.size() : -1; }
+
+void ttsh_batch_destroy(ttsh_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto& g : b->groups) {
+    if (g.args_dev) cudaFree(g.args_dev);
+    if (g.branch) cudaStreamDestroy(g.branch);
+    if (g.join) cudaEventDestroy(g.join);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->capture) cudaStreamDestroy(b->capture);
+  delete b;
 }
 
 ttsh_status ttsh_synchronize(ttsh_domain* d) {

@@ -35,14 +35,21 @@ using SpecFn = cudaError_t (*)(const DomainDev&, int nbins, cudaStream_t);
 using BlocksFn = int (*)(int kind);
 
 using StepFn = cudaError_t (*)(const DomainDev&, cudaStream_t);
+// Batched launch: `args` is a device array of ndom per-domain kernel argument blocks.
+using BatchFn = cudaError_t (*)(const void* args, int ndom, cudaStream_t);
+using PrepareFn = cudaError_t (*)();
 
 // One tile shape of a step kernel: rows per block (row pass only) and points per thread of
-// the register butterflies.
+// the register butterflies.  `batched` / `prepare` are set for grids up to kMaxBatchN.
 struct StepVariant {
   StepFn fn;
+  BatchFn batched;
+  PrepareFn prepare;   // sets the batched kernel's attributes (call before graph capture)
   int rows;
   int pe;
 };
+
+constexpr int kMaxBatchN = 1024;
 
 constexpr int kMaxVariants = 8;
 
@@ -54,6 +61,8 @@ struct SizeOps {
   int n_row_variants, n_col_variants;           // entry 0 is the default tile shape
   StepVariant row_step[kMaxVariants];
   StepVariant col_step[kMaxVariants];
+  int args_bytes;                                    // size of one kernel argument block
+  void (*pack_args)(const DomainDev&, void* dst);    // host copy of a domain's argument block
 };
 
 // Per translation unit registries; return false if the TU does not hold size n.

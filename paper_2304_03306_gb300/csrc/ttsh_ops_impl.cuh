@@ -4,6 +4,7 @@
 #pragma once
 
 #include <atomic>
+#include <cstring>
 
 #include "ttsh_kernels.cuh"
 #include "ttsh_ops.h"
@@ -102,12 +103,50 @@ static cudaError_t launch_spec(const DomainDev& d, int nbins, cudaStream_t s) {
 }
 
 template <typename T, int N, int R, int PE>
+static cudaError_t launch_row_batched(const void* args, int ndom, cudaStream_t s) {
+  using Geo = RowGeo<T, N, ROW_STEP, R, PE>;
+  row_kernel_batched<T, N, ROW_STEP, R, PE><<<dim3(N / R, ndom), Geo::NT, Geo::SMEM, s>>>(
+      static_cast<const Args<T>*>(args));
+  return cudaGetLastError();
+}
+
+template <typename T, int N, int R, int PE>
+static cudaError_t prepare_row_batched() {
+  static std::atomic<int> done{0};
+  return set_smem(row_kernel_batched<T, N, ROW_STEP, R, PE>, RowGeo<T, N, ROW_STEP, R, PE>::SMEM, done);
+}
+
+template <typename T, int N, int PE>
+static cudaError_t launch_col_batched(const void* args, int ndom, cudaStream_t s) {
+  using Geo = ColGeo<T, N, COL_STEP, PE>;
+  col_kernel_batched<T, N, COL_STEP, PE><<<dim3(Geo::H, ndom), Geo::NT, Geo::SMEM, s>>>(
+      static_cast<const Args<T>*>(args));
+  return cudaGetLastError();
+}
+
+template <typename T, int N, int PE>
+static cudaError_t prepare_col_batched() {
+  static std::atomic<int> done{0};
+  return set_smem(col_kernel_batched<T, N, COL_STEP, PE>, ColGeo<T, N, COL_STEP, PE>::SMEM, done);
+}
+
+template <typename T>
+static void pack_args(const DomainDev& d, void* dst) {
+  const Args<T> a = make_args<T>(d);
+  memcpy(dst, &a, sizeof(a));
+}
+
+template <typename T, int N, int R, int PE>
 static void add_row_variant(SizeOps& o) {
   if constexpr (RowGeo<T, N, ROW_STEP, R, PE>::VALID && (N >= 64 || (R == default_rows<T, N>() && PE == default_row_pe<T, N>()))) {
     for (int i = 0; i < o.n_row_variants; ++i)
       if (o.row_step[i].rows == R && o.row_step[i].pe == cmin(PE, N / 2)) return;   // same shape
-    if (o.n_row_variants < kMaxVariants)
-      o.row_step[o.n_row_variants++] = StepVariant{&launch_row_kind<T, N, ROW_STEP, R, PE>, R, cmin(PE, N / 2)};
+    StepVariant v{&launch_row_kind<T, N, ROW_STEP, R, PE>, nullptr, nullptr, R, cmin(PE, N / 2)};
+    if constexpr (N <= kMaxBatchN) {
+      v.batched = &launch_row_batched<T, N, R, PE>;
+      v.prepare = &prepare_row_batched<T, N, R, PE>;
+    }
+    if (o.n_row_variants < kMaxVariants) o.row_step[o.n_row_variants++] = v;
   }
 }
 
@@ -116,8 +155,12 @@ static void add_col_variant(SizeOps& o) {
   if constexpr (ColGeo<T, N, COL_STEP, PE>::VALID && (N >= 64 || PE == default_col_pe<T, N>())) {
     for (int i = 0; i < o.n_col_variants; ++i)
       if (o.col_step[i].pe == cmin(PE, N)) return;
-    if (o.n_col_variants < kMaxVariants)
-      o.col_step[o.n_col_variants++] = StepVariant{&launch_col_mode<T, N, COL_STEP, PE>, 1, cmin(PE, N)};
+    StepVariant v{&launch_col_mode<T, N, COL_STEP, PE>, nullptr, nullptr, 1, cmin(PE, N)};
+    if constexpr (N <= kMaxBatchN) {
+      v.batched = &launch_col_batched<T, N, PE>;
+      v.prepare = &prepare_col_batched<T, N, PE>;
+    }
+    if (o.n_col_variants < kMaxVariants) o.col_step[o.n_col_variants++] = v;
   }
 }
 
@@ -130,6 +173,8 @@ static SizeOps make_ops() {
   o.row_blocks = &row_blocks<T, N>;
   o.n_row_variants = 0;
   o.n_col_variants = 0;
+  o.args_bytes = (int)sizeof(Args<T>);
+  o.pack_args = &pack_args<T>;
   add_row_variant<T, N, default_rows<T, N>(), default_row_pe<T, N>()>(o);
   add_col_variant<T, N, default_col_pe<T, N>()>(o);
   if constexpr (sizeof(T) == 4) {

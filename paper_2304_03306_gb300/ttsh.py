@@ -75,6 +75,11 @@ def load_library(path: str = LIB_PATH):
         "ttsh_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
         "ttsh_get_plan": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
         "ttsh_set_plan": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+        "ttsh_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P, ctypes.POINTER(_P)]),
+        "ttsh_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+        "ttsh_batch_synchronize": (ctypes.c_int, [_P]),
+        "ttsh_batch_groups": (ctypes.c_int32, [_P]),
+        "ttsh_batch_destroy": (None, [_P]),
         "ttsh_step_count": (ctypes.c_int64, [_P]),
         "ttsh_step_noalloc": (ctypes.c_int, [ctypes.POINTER(ttsh_params), _P, _P, _P, ctypes.c_int64, _P]),
         "ttsh_last_error": (ctypes.c_char_p, []),
@@ -220,6 +225,58 @@ def ttsh_get_plan(h) -> dict:
 
 def ttsh_set_plan(h, row_variant: int, col_variant: int):
     _check(load_library().ttsh_set_plan(h, int(row_variant), int(col_variant)))
+
+
+def ttsh_batch_create(handles, stream: int | None = None):
+    arr = (_P * len(handles))(*[h.value if isinstance(h, _P) else h for h in handles])
+    b = _P()
+    _check(load_library().ttsh_batch_create(arr, len(handles), stream, ctypes.byref(b)))
+    return b
+
+
+def ttsh_batch_step(b, nsteps: int):
+    _check(load_library().ttsh_batch_step(b, int(nsteps)))
+
+
+def ttsh_batch_synchronize(b):
+    _check(load_library().ttsh_batch_synchronize(b))
+
+
+def ttsh_batch_groups(b) -> int:
+    return int(load_library().ttsh_batch_groups(b))
+
+
+def ttsh_batch_destroy(b):
+    load_library().ttsh_batch_destroy(b)
+
+
+class Batch:
+    """Lock-step stepping of several Domain objects (they must stay alive)."""
+
+    def __init__(self, domains, stream: int | None = None):
+        self.domains = list(domains)
+        self.b = ttsh_batch_create([d.h for d in self.domains], stream)
+
+    def step(self, nsteps: int):
+        ttsh_batch_step(self.b, nsteps)
+
+    def synchronize(self):
+        ttsh_batch_synchronize(self.b)
+
+    @property
+    def groups(self) -> int:
+        return ttsh_batch_groups(self.b)
+
+    def close(self):
+        if self.b:
+            ttsh_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def ttsh_synchronize(h):

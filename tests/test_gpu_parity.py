@@ -325,3 +325,70 @@ def test_autotune_selects_a_valid_plan_and_keeps_state(T):
     assert rel(w, O.vorticity(ref)) <= TOL[32]
     with pytest.raises(T.TTSHError):
         dom.set_plan(plan["n_row_variants"], 0)
+
+
+# ------------------------------------------------------------------ batched stepping
+
+def _domain_copy(T, mask, n, dx, prec, vx, vy):
+    d = T.Domain(mask, n, dx, precision=prec)
+    d.set_velocity(vx, vy)
+    return d
+
+
+def test_batch_equals_individual_domains_bit_for_bit(T):
+    specs = [(64, 0.25, 32, "c", 5.2), (64, 0.25, 32, "c", 5.0), (128, 0.16, 32, "c", 5.3),
+             (128, 0.16, 64, "c", 5.3), (256, 0.08, 32, "d", 3.0), (32, 0.5, 64, "c", 5.0)]
+    batched, alone = [], []
+    for i, (n, dx, prec, shape, R) in enumerate(specs):
+        mask = ti.circle_mask(n, dx, R) if shape == "c" else ti.dumbbell_mask(n, dx, R, 1.4 * R)
+        vx, vy = ti.noise_velocity(mask, 40 + i, 0.3)
+        batched.append(_domain_copy(T, mask, n, dx, prec, vx, vy))
+        alone.append(_domain_copy(T, mask, n, dx, prec, vx, vy))
+    b = T.Batch(batched)
+    assert b.groups == 5        # the two 64^2 float circles share a launch group
+    b.step(70)                  # two graph replays of 32 steps + 6 eager steps
+    b.synchronize()
+    for d in alone:
+        d.step(70)
+    for d1, d2 in zip(batched, alone):
+        assert d1.steps == d2.steps == 70
+        w1, v1 = d1.spectral_state()
+        w2, v2 = d2.spectral_state()
+        assert np.array_equal(w1, w2) and np.array_equal(v1, v2)
+    b.close()
+
+
+def test_batch_sweep_workload_matches_oracle_on_samples(T):
+    doms = ti.sweep_domains()
+    assert len(doms) == 48
+    assert sum(d["n"] ** 2 for d in doms) == 3342336
+    objs = []
+    for d in doms:
+        o = T.Domain(d["mask"], d["n"], d["dx"], precision=32)
+        vx, vy = ti.noise_velocity(d["mask"], d["seed"], 0.3)
+        o.set_velocity(vx, vy)
+        objs.append(o)
+    b = T.Batch(objs)
+    b.step(10)
+    b.synchronize()
+    for idx in (0, 13, 22, 40):      # a 128^2, 256^2 and 512^2 circle and a dumbbell
+        d = doms[idx]
+        p = O.Params(n=d["n"], dx=d["dx"])
+        vx, vy = ti.noise_velocity(d["mask"], d["seed"], 0.3)
+        ref = O.run(O.project_velocity(vx, vy, p), O.process_mask(d["mask"]), p, 10)
+        gvx, gvy, gw = objs[idx].fields()
+        assert rel(gw, O.vorticity(ref)) <= TOL[32], d["name"]
+        assert rel(np.stack([gvx, gvy]), np.stack([ref.vx, ref.vy])) <= TOL[32], d["name"]
+    b.close()
+
+
+def test_batch_rejects_bad_input(T):
+    m = ti.circle_mask(64, 0.25, 5.0)
+    d = T.Domain(m, 64, 0.25, precision=32)
+    with pytest.raises(T.TTSHError) as e:
+        T.Batch([d, d])
+    assert e.value.status == T.TTSH_E_INVALID
+    big = T.Domain(np.zeros((2048, 2048), np.uint8), 2048, 0.02, precision=32)
+    with pytest.raises(T.TTSHError) as e:
+        T.Batch([d, big])
+    assert e.value.status == T.TTSH_E_UNSUPPORTED

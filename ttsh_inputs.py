@@ -91,3 +91,25 @@ WORKLOADS = {
     "circle4096_turbulent": dict(n=4096, dx=0.01, radius=12.0, seed=4, steps=1000),
     "circle8192_paper_grid": dict(n=8192, dx=0.005, radius=12.0, seed=4, steps=100),
 }
+
+
+def sweep_domains():
+    """The 48-domain sweep of the batched workload: 24 circles (12 radii across the
+    stationary, oscillatory and chaotic regimes, each as a forward and a backward member of a
+    hysteresis sweep) and 24 dumbbells (R in {2.8, pi, 3.5} x D/R in 8 steps from 1.0 to 1.9),
+    on 128^2 to 512^2 grids.  Returns a list of dicts (name, n, dx, mask, seed)."""
+    out = []
+    circles = [(r, 128, 0.16) for r in (5.0, 5.1, 5.2, 5.25, 5.3, 5.35)] + \
+              [(r, 256, 0.08) for r in (5.4, 5.6, 5.8, 6.4)] + [(r, 512, 0.08) for r in (7.2, 8.0)]
+    i = 0
+    for direction in ("forward", "backward"):
+        for r, n, dx in circles:
+            out.append(dict(name=f"circle R={r} ({direction})", n=n, dx=dx,
+                            mask=circle_mask(n, dx, r), seed=100 + i))
+            i += 1
+    for r in (2.8, float(np.pi), 3.5):
+        for ratio in np.linspace(1.0, 1.9, 8):
+            out.append(dict(name=f"dumbbell R={r:.4f} D/R={ratio:.3f}", n=256, dx=0.08,
+                            mask=dumbbell_mask(256, 0.08, r, ratio * r), seed=100 + i))
+            i += 1
+    return out
