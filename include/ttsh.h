@@ -76,6 +76,7 @@ typedef struct {
 
 typedef struct ttsh_domain ttsh_domain;
 typedef struct ttsh_batch ttsh_batch;
+typedef struct ttsh_fno ttsh_fno;
 
 /* Fill *p with the Table I constants (Appendix B).  Never fails. */
 void ttsh_default_params(ttsh_params* p);
@@ -206,6 +207,57 @@ ttsh_status ttsh_batch_step(ttsh_batch* b, int64_t nsteps);
 ttsh_status ttsh_batch_synchronize(ttsh_batch* b);
 int32_t ttsh_batch_groups(const ttsh_batch* b);   /* number of launch groups, -1 if NULL */
 void ttsh_batch_destroy(ttsh_batch* b);           /* NULL is a no-op; domains are untouched */
+
+/* Spectral restriction of a fine domain's state onto a coarse domain covering the same box
+ * (n_fine * dx_fine == n_coarse * dx_coarse, n_coarse <= n_fine, same precision): the coarse
+ * unitary coefficients are the fine ones times n_coarse/n_fine on the coarse 1/2-rule disc,
+ * so the coarse real-space fields are the band-limited fine fields sampled on the coarse
+ * grid.  Used to build the learned corrector's training targets.  Resets the coarse step
+ * counter; asynchronous on the coarse domain's stream (waits for the fine stream first). */
+ttsh_status ttsh_restrict(const ttsh_domain* fine, ttsh_domain* coarse);
+
+/* ---------------------------------------------------------------------------------------
+ * Learned corrector (not in the paper): a Fourier neural operator (Li et al., ICLR 2021)
+ * that corrects the vorticity after a coarse solver step taken with a larger time step.
+ *   x (B*n*n x 4): per point (omega, v_x, v_y, K) times in_scale, indexed [b][y][x][c]
+ *   lift 4 -> C, then `layers` blocks z = h W + b + SpectralConv(h), h' = GELU(z) (none after
+ *   the last block), projection C -> 1: the predicted omega correction times out_scale.
+ *   SpectralConv keeps kx < modes and ky in {0..modes-1} U {n-modes..n-1} of rfft2(h) and
+ *   mixes channels per kept mode with a complex C x C matrix, then irfft2.
+ * Weights: FP32 master copies (flat vector, order: Wp[4][C], bp[C], per block Wr[2m][m][C][C],
+ * Wi[2m][m][C][C], W[C][C], b[C], then Wq[C], bq) used as BF16 by the kernels, FP32
+ * accumulation; channel mixing on the tensor cores.  All device pointers below are the
+ * caller's (FP32).  Width must be 32 and in_channels 4 (TTSH_E_UNSUPPORTED otherwise). */
+typedef struct {
+  int32_t n, width, modes, layers, in_channels, max_batch;
+} ttsh_fno_config;
+
+/* Seeded initialisation (SplitMix64): pointwise weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)),
+ * spectral weights U(0, 1/C^2), biases 0.  Allocates its parameters and activations for up to
+ * max_batch samples.  Runs on `stream`. */
+ttsh_status ttsh_fno_create(const ttsh_fno_config* cfg, uint64_t seed, void* stream, ttsh_fno** out);
+void ttsh_fno_destroy(ttsh_fno* f);
+int64_t ttsh_fno_num_params(const ttsh_fno* f);
+ttsh_status ttsh_fno_get_params(ttsh_fno* f, float* host);      /* num_params floats */
+ttsh_status ttsh_fno_set_params(ttsh_fno* f, const float* host);
+ttsh_status ttsh_fno_set_scales(ttsh_fno* f, const float* in_scale /* 4 */, float out_scale);
+/* y (B*n*n) = network(x); asynchronous. */
+ttsh_status ttsh_fno_forward(ttsh_fno* f, const float* x, float* y, int32_t batch);
+/* Mean squared error of network(x) against target (B*n*n) and its gradient with respect to
+ * every parameter (kept on the device for ttsh_fno_adam_step; copied to grad_host when
+ * non-NULL).  Synchronises. */
+ttsh_status ttsh_fno_loss_grad(ttsh_fno* f, const float* x, const float* target, int32_t batch, double* loss,
+                               float* grad_host);
+/* One Adam step (Kingma & Ba 2015, bias-corrected) with the last gradient. */
+ttsh_status ttsh_fno_adam_step(ttsh_fno* f, float lr, float beta1, float beta2, float eps);
+/* Network input of sample `sample` from a domain's current state (domain n == network n). */
+ttsh_status ttsh_fno_features(ttsh_fno* f, ttsh_domain* d, float* x, int32_t sample);
+/* Training target of sample `sample`: (omega(truth) - omega(base)) * out_scale. */
+ttsh_status ttsh_fno_residual(ttsh_fno* f, ttsh_domain* truth, ttsh_domain* base, float* target, int32_t sample);
+/* Apply the corrector to a domain: omega += network(features)/out_scale, projected onto the
+ * 1/2-rule disc (Hermitian, zero mean) as Algorithm 1's post-processing does.  scratch: a
+ * device buffer of 5*n*n floats. */
+ttsh_status ttsh_fno_correct(ttsh_fno* f, ttsh_domain* d, float* scratch);
 
 /* Block the host until the domain's stream is idle; reports deferred CUDA errors. */
 ttsh_status ttsh_synchronize(ttsh_domain* d);

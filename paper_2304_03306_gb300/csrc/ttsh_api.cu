@@ -294,6 +294,41 @@ cudaError_t launch_spectrum_reduce(const double* colhist, int ncols, int nbins, 
 }  // namespace ttsh
 
 
+namespace ttsh {
+const DomainDev* domain_dev(const ttsh_domain* d) { return &d->dev; }
+cudaStream_t domain_stream(const ttsh_domain* d) { return d->stream; }
+int domain_precision(const ttsh_domain* d) { return d->p.precision; }
+int domain_n(const ttsh_domain* d) { return d->n; }
+double domain_dx(const ttsh_domain* d) { return d->p.dx; }
+int domain_fields_to_staging(ttsh_domain* d) { return run_row(d, K_ROW_INV_FIELDS, d->stream); }
+int domain_add_vorticity_from_staging(ttsh_domain* d) {
+  ttsh_status st = run_row(d, K_ROW_FWD_MASK, d->stream);   // one real field forward
+  if (st != TTSH_OK) return st;
+  return run_col(d, K_COL_ADDW, d->stream);
+}
+
+// Spectral restriction of a fine state onto a coarse grid of the same box: the coarse
+// unitary coefficients are the fine ones times Nc/Nf on the coarse 1/2-rule disc.
+template <typename T>
+__global__ void restrict_kernel(const cplx<T>* __restrict__ wf, const T* __restrict__ vf, int nf,
+                                cplx<T>* __restrict__ wc, T* __restrict__ vc, int nc) {
+  const int Mf = nf / 4, NKf = 2 * Mf + 1, Mc = nc / 4, NKc = 2 * Mc + 1, Hc = Mc + 1;
+  const T s = (T)nc / (T)nf;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Hc * NKc) return;
+  const int kx = i / NKc, j = i % NKc;
+  const int ky = j <= Mc ? j : j - NKc;
+  const int jf = ky >= 0 ? ky : ky + NKf;
+  cplx<T> w = wf[(size_t)kx * NKf + jf];
+  if (kx * kx + ky * ky > Mc * Mc) w = mk<T>(0, 0);
+  wc[i] = w * s;
+  if (i == 0) {
+    vc[0] = vf[0] * s;
+    vc[1] = vf[1] * s;
+  }
+}
+}  // namespace ttsh
+
 // ---------------------------------------------------------------------------------------
 // Batched stepping: domains grouped by (precision, n, plan); one launch per pass per group
 // advances every domain of the group (blockIdx.y = domain).  Groups are independent, so each
@@ -826,6 +861,29 @@ void ttsh_batch_destroy(ttsh_batch* b) {
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->capture) cudaStreamDestroy(b->capture);
   delete b;
+}
+
+ttsh_status ttsh_restrict(const ttsh_domain* fine, ttsh_domain* coarse) {
+  if (!fine || !coarse) return fail(TTSH_E_INVALID, "NULL domain");
+  if (fine->p.precision != coarse->p.precision) return fail(TTSH_E_INVALID, "precisions differ");
+  if (coarse->n > fine->n) return fail(TTSH_E_INVALID, "coarse grid is finer than the fine grid");
+  const double lf = fine->n * fine->p.dx, lc = coarse->n * coarse->p.dx;
+  if (std::fabs(lf - lc) > 1e-12 * lf) return fail(TTSH_E_INVALID, "domains cover different boxes");
+  TTSH_CUDA(cudaStreamSynchronize(fine->stream), "fine stream");
+  const int total = coarse->H * coarse->NK;
+  if (coarse->elt == sizeof(float))
+    ttsh::restrict_kernel<float><<<(total + 255) / 256, 256, 0, coarse->stream>>>(
+        (const ttsh::cplx<float>*)fine->dev.what, (const float*)fine->dev.vmean, fine->n,
+        (ttsh::cplx<float>*)coarse->dev.what, (float*)coarse->dev.vmean, coarse->n);
+  else
+    ttsh::restrict_kernel<double><<<(total + 255) / 256, 256, 0, coarse->stream>>>(
+        (const ttsh::cplx<double>*)fine->dev.what, (const double*)fine->dev.vmean, fine->n,
+        (ttsh::cplx<double>*)coarse->dev.what, (double*)coarse->dev.vmean, coarse->n);
+  TTSH_CUDA(cudaGetLastError(), "restrict kernel");
+  ttsh_status st = run_col(coarse, ttsh::K_COL_PROLOGUE, coarse->stream);
+  if (st != TTSH_OK) return st;
+  coarse->steps = 0;
+  return TTSH_OK;
 }
 
 ttsh_status ttsh_synchronize(ttsh_domain* d) {

@@ -1,0 +1,932 @@
+// ttsh_fno.cu - learned corrector: a Fourier neural operator (FNO) that corrects a coarse,
+// 4x-larger-time-step solver step, with forward and backward kernels for training on the GPU.
+//
+// The network (Li et al., ICLR 2021): lift (Cin -> C, bias), L Fourier layers
+//   z = h W + b + SpectralConv(h),  h' = GELU(z) (no GELU after the last layer),
+// and a projection C -> 1.  SpectralConv = irfft2(P(W_modes * P^T(rfft2(h)))) keeping kx < m
+// and ky in {0..m-1} U {n-m..n-1}, one complex C x C matrix per kept mode.
+//
+// Arithmetic: learned weights are held as FP32 master copies and used in BF16 by the kernels;
+// every product accumulates in FP32.  The channel-mixing layers (h W, and dz W^T in the
+// backward pass) run on the tensor cores (mma.sync m16n8k16 BF16 -> FP32, fused bias /
+// residual / GELU epilogue).  The transforms restricted to the kept modes are exact DFT
+// matrices applied by an FP32 batched GEMM (2m x n per row and per column, cheaper than a full
+// FFT when m << n), and the per-mode complex mixing reads BF16 weights with FP32 sums.
+// Gradients use fixed-order partial sums, so repeated calls give identical bits.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ttsh.h"
+#include "ttsh_ops.h"
+
+namespace fno_dev {
+
+// ---------------------------------------------------------------------------------------
+// FP32 batched GEMM: C[b] = alpha * op(A[b]) * op(B[b]) + beta * C[b] (row-major, 64x64 tiles)
+// ---------------------------------------------------------------------------------------
+struct Gemm {
+  int M, N, K, batch;
+  const float* A;
+  long long lda, sA;
+  const float* B;
+  long long ldb, sB;
+  float* C;
+  long long ldc, sC;
+  float alpha, beta;
+};
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) sgemm_kernel(Gemm g) {
+  __shared__ float As[16][64 + 4];
+  __shared__ float Bs[16][64 + 4];
+  const long long bz = blockIdx.z;
+  const float* A = g.A + bz * g.sA;
+  const float* B = g.B + bz * g.sB;
+  float* C = g.C + bz * g.sC;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < g.K; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int mm, kk;
+      if (TA) { mm = e & 63; kk = e >> 6; } else { kk = e & 15; mm = e >> 4; }
+      const int m = m0 + mm, k = k0 + kk;
+      float v = 0.f;
+      if (m < g.M && k < g.K) v = TA ? A[(long long)k * g.lda + m] : A[(long long)m * g.lda + k];
+      As[kk][mm] = v;
+    }
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int nn, kk;
+      if (TB) { kk = e & 15; nn = e >> 4; } else { nn = e & 63; kk = e >> 6; }
+      const int n = n0 + nn, k = k0 + kk;
+      float v = 0.f;
+      if (n < g.N && k < g.K) v = TB ? B[(long long)n * g.ldb + k] : B[(long long)k * g.ldb + n];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= g.N) continue;
+      float* c = C + (long long)m * g.ldc + n;
+      const float prev = g.beta != 0.f ? g.beta * *c : 0.f;
+      *c = g.alpha * acc[i][j] + prev;
+    }
+  }
+}
+
+cudaError_t sgemm(bool ta, bool tb, int M, int N, int K, int batch, float alpha, const float* A,
+                  long long lda, long long sA, const float* B, long long ldb, long long sB, float beta,
+                  float* C, long long ldc, long long sC, cudaStream_t s) {
+  Gemm g{M, N, K, batch, A, lda, sA, B, ldb, sB, C, ldc, sC, alpha, beta};
+  dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
+  if (ta && tb) sgemm_kernel<true, true><<<grid, 256, 0, s>>>(g);
+  else if (ta) sgemm_kernel<true, false><<<grid, 256, 0, s>>>(g);
+  else if (tb) sgemm_kernel<false, true><<<grid, 256, 0, s>>>(g);
+  else sgemm_kernel<false, false><<<grid, 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Tensor-core channel mixing: out[p][o] = sum_i A[p][i] Bt[o][i] (+ epilogue), C = 32
+// ---------------------------------------------------------------------------------------
+constexpr int CW = 32;   // width the tensor-core kernels are written for
+
+__device__ __forceinline__ void mma16816(float* d, const unsigned* a, const unsigned* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+enum { EPI_FWD = 0, EPI_FWD_LAST = 1, EPI_BWD = 2 };
+
+struct PwArgs {
+  const __nv_bfloat16* A;   // P x 32
+  const __nv_bfloat16* Bt;  // 32 x 32, [o][i]
+  const float* bias;        // 32 (forward) or nullptr
+  const float* add;         // P x 32 residual added to the product
+  float* out;               // P x 32: z (forward) or dh (backward)
+  float* h;                 // P x 32: GELU(z) (forward)
+  __nv_bfloat16* hb;        // P x 32: GELU(z) in BF16 (forward)
+  long long P;
+};
+
+// One warp computes 16 rows x 32 columns (4 n-tiles x 2 k-steps of m16n8k16).
+template <int EPI>
+__global__ void __launch_bounds__(256) pointwise_mma_kernel(PwArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const long long row0 = ((long long)blockIdx.x * 8 + warp) * 16;
+  if (row0 >= a.P) return;
+  const unsigned* A32 = reinterpret_cast<const unsigned*>(a.A);
+  const unsigned* B32 = reinterpret_cast<const unsigned*>(a.Bt);
+  unsigned af[2][4];
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks) {
+    const long long r0 = (row0 + g) * CW + ks * 16 + 2 * t, r1 = (row0 + g + 8) * CW + ks * 16 + 2 * t;
+    af[ks][0] = A32[r0 >> 1];
+    af[ks][1] = A32[r1 >> 1];
+    af[ks][2] = A32[(r0 + 8) >> 1];
+    af[ks][3] = A32[(r1 + 8) >> 1];
+  }
+  float d[4][4];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d[nt][q] = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const int b0 = (nt * 8 + g) * CW + ks * 16 + 2 * t;
+      unsigned bf[2] = {B32[b0 >> 1], B32[(b0 + 8) >> 1]};
+      mma16816(d[nt], af[ks], bf);
+    }
+  }
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const long long p = row0 + g + 8 * half;
+      const int o = nt * 8 + 2 * t;
+      const long long idx = p * CW + o;
+      float v0 = d[nt][2 * half], v1 = d[nt][2 * half + 1];
+      const float2 ad = *reinterpret_cast<const float2*>(a.add + idx);
+      v0 += ad.x;
+      v1 += ad.y;
+      if (EPI != EPI_BWD) {
+        v0 += a.bias[o];
+        v1 += a.bias[o + 1];
+      }
+      *reinterpret_cast<float2*>(a.out + idx) = make_float2(v0, v1);
+      if (EPI == EPI_FWD) {
+        const float h0 = gelu(v0), h1 = gelu(v1);
+        *reinterpret_cast<float2*>(a.h + idx) = make_float2(h0, h1);
+        *reinterpret_cast<__nv_bfloat162*>(a.hb + idx) = __floats2bfloat162_rn(h0, h1);
+      } else if (EPI == EPI_FWD_LAST) {
+        *reinterpret_cast<float2*>(a.h + idx) = make_float2(v0, v1);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Elementwise kernels
+// ---------------------------------------------------------------------------------------
+// h0 = x Wp + bp (Cin inputs), FP32 and BF16 copies
+__global__ void lift_kernel(const float* __restrict__ x, const float* __restrict__ Wp, const float* __restrict__ bp,
+                            int cin, long long P, float* __restrict__ h, __nv_bfloat16* __restrict__ hb) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P * CW) return;
+  const long long p = i / CW;
+  const int c = (int)(i % CW);
+  float acc = bp[c];
+  for (int k = 0; k < cin; ++k) acc = fmaf(x[p * cin + k], Wp[k * CW + c], acc);
+  h[i] = acc;
+  hb[i] = __float2bfloat16_rn(acc);
+}
+
+// out[p] = h[p] . Wq + bq; with a target: dout = 2 (out - t) / npts, dh = dout Wq, and
+// per-block partial sums of (out - t)^2
+__global__ void __launch_bounds__(256) project_kernel(const float* __restrict__ h, const float* __restrict__ Wq,
+                                                      const float* __restrict__ bq, long long P, float* __restrict__ out,
+                                                      const float* __restrict__ target, float* __restrict__ dout,
+                                                      float* __restrict__ dh, double* __restrict__ lpart) {
+  __shared__ double red[256];
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double sq = 0.0;
+  if (p < P) {
+    float acc = bq[0];
+#pragma unroll
+    for (int c = 0; c < CW; ++c) acc = fmaf(h[p * CW + c], Wq[c], acc);
+    out[p] = acc;
+    if (target) {
+      const float r = acc - target[p];
+      sq = (double)r * r;
+      const float g = 2.f * r / (float)P;
+      dout[p] = g;
+#pragma unroll
+      for (int c = 0; c < CW; ++c) dh[p * CW + c] = g * Wq[c];
+    }
+  }
+  if (!target) return;
+  red[threadIdx.x] = sq;
+  __syncthreads();
+  for (int s = 128; s >= 1; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) lpart[blockIdx.x] = red[0];
+}
+
+// dz = dh * GELU'(z) (FP32 and BF16); for the last layer (no GELU) dz = dh
+__global__ void gelu_bwd_kernel(const float* __restrict__ dh, const float* __restrict__ z, long long n, int act,
+                                float* __restrict__ dz, __nv_bfloat16* __restrict__ dzb) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float v = act ? dh[i] * gelu_grad(z[i]) : dh[i];
+  dz[i] = v;
+  dzb[i] = __float2bfloat16_rn(v);
+}
+
+// Partial weight gradients over a chunk of points: part[blk][i*cd + o] = sum_p A[p][i] D[p][o],
+// part[blk][ca*cd + o] = sum_p D[p][o]  (ca, cd <= 32; fixed order)
+__global__ void __launch_bounds__(256) wgrad_partial_kernel(const float* __restrict__ A, int ca,
+                                                            const float* __restrict__ D, int cd, long long P,
+                                                            int chunk, float* __restrict__ part) {
+  __shared__ float As[64][33];
+  __shared__ float Ds[64][33];
+  const int nout = ca * cd + cd;
+  float acc[5] = {0, 0, 0, 0, 0};   // up to 5 outputs per thread (1056 / 256 -> 5)
+  const long long p0 = (long long)blockIdx.x * chunk;
+  const long long p1 = p0 + chunk < P ? p0 + chunk : P;
+  for (long long pb = p0; pb < p1; pb += 64) {
+    for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+      const int r = e >> 5, c = e & 31;
+      const long long p = pb + r;
+      As[r][c] = (p < p1 && c < ca) ? A[p * ca + c] : 0.f;
+      Ds[r][c] = (p < p1 && c < cd) ? D[p * cd + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const int o = threadIdx.x + 256 * q;
+      if (o < nout) {
+        const int i = o / cd, j = o % cd;
+        float s = 0.f;
+        if (i < ca)
+          for (int r = 0; r < 64; ++r) s = fmaf(As[r][i], Ds[r][j], s);
+        else
+          for (int r = 0; r < 64; ++r) s += Ds[r][j];
+        acc[q] += s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    const int o = threadIdx.x + 256 * q;
+    if (o < nout) part[(long long)blockIdx.x * nout + o] = acc[q];
+  }
+}
+
+// grad[w_off + i*cd + o] = sum_blk part (then bias at b_off + o); fixed order over blocks
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, int nblk, int ca, int cd,
+                                    float* __restrict__ gw, float* __restrict__ gb) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nout = ca * cd + cd;
+  if (o >= nout) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(long long)b * nout + o];
+  if (o < ca * cd) gw[o] = (float)s;
+  else gb[o - ca * cd] = (float)s;
+}
+
+// Mode mixing, forward: Y[b][mode][o] = sum_i W[mode][i][o] H[b][mode][i] (complex, BF16 weights)
+__global__ void __launch_bounds__(CW) modemix_fwd_kernel(const float* __restrict__ Hr, const float* __restrict__ Hi,
+                                                         const __nv_bfloat16* __restrict__ Wr,
+                                                         const __nv_bfloat16* __restrict__ Wi, int nmodes, int B,
+                                                         float* __restrict__ Yr, float* __restrict__ Yi) {
+  __shared__ float wr[CW][CW + 1], wi[CW][CW + 1], hr[CW], hi[CW];
+  const int mode = blockIdx.x, o = threadIdx.x;
+  for (int i = 0; i < CW; ++i) {
+    wr[i][o] = __bfloat162float(Wr[((long long)mode * CW + i) * CW + o]);
+    wi[i][o] = __bfloat162float(Wi[((long long)mode * CW + i) * CW + o]);
+  }
+  for (int b = 0; b < B; ++b) {
+    const long long base = ((long long)b * nmodes + mode) * CW;
+    __syncthreads();
+    hr[o] = Hr[base + o];
+    hi[o] = Hi[base + o];
+    __syncthreads();
+    float yr = 0.f, yi = 0.f;
+    for (int i = 0; i < CW; ++i) {
+      yr = fmaf(wr[i][o], hr[i], fmaf(-wi[i][o], hi[i], yr));
+      yi = fmaf(wr[i][o], hi[i], fmaf(wi[i][o], hr[i], yi));
+    }
+    Yr[base + o] = yr;
+    Yi[base + o] = yi;
+  }
+}
+
+// Mode mixing, backward: dH = W^H dY per mode; dW[i][o] = sum_b dY_o conj(H_i)
+__global__ void __launch_bounds__(256) modemix_bwd_kernel(const float* __restrict__ Hr, const float* __restrict__ Hi,
+                                                          const float* __restrict__ dYr, const float* __restrict__ dYi,
+                                                          const __nv_bfloat16* __restrict__ Wr,
+                                                          const __nv_bfloat16* __restrict__ Wi, int nmodes, int B,
+                                                          float* __restrict__ dHr, float* __restrict__ dHi,
+                                                          float* __restrict__ gWr, float* __restrict__ gWi) {
+  __shared__ float wr[CW][CW + 1], wi[CW][CW + 1];
+  __shared__ float hr[CW], hi[CW], yr[CW], yi[CW];
+  const int mode = blockIdx.x, tid = threadIdx.x;
+  for (int e = tid; e < CW * CW; e += 256) {
+    const int i = e / CW, o = e % CW;
+    wr[i][o] = __bfloat162float(Wr[(long long)mode * CW * CW + e]);
+    wi[i][o] = __bfloat162float(Wi[(long long)mode * CW * CW + e]);
+  }
+  float ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
+  for (int b = 0; b < B; ++b) {
+    const long long base = ((long long)b * nmodes + mode) * CW;
+    __syncthreads();
+    if (tid < CW) {
+      hr[tid] = Hr[base + tid];
+      hi[tid] = Hi[base + tid];
+      yr[tid] = dYr[base + tid];
+      yi[tid] = dYi[base + tid];
+    }
+    __syncthreads();
+    if (tid < CW) {   // dH_i = sum_o conj(W_io) dY_o
+      const int i = tid;
+      float sr = 0.f, si = 0.f;
+      for (int o = 0; o < CW; ++o) {
+        sr = fmaf(wr[i][o], yr[o], fmaf(wi[i][o], yi[o], sr));
+        si = fmaf(wr[i][o], yi[o], fmaf(-wi[i][o], yr[o], si));
+      }
+      dHr[base + i] = sr;
+      dHi[base + i] = si;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      const int i = e / CW, o = e % CW;
+      ar[q] = fmaf(yr[o], hr[i], fmaf(yi[o], hi[i], ar[q]));
+      ai[q] = fmaf(yi[o], hr[i], fmaf(-yr[o], hi[i], ai[q]));
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int e = tid + 256 * q;
+    gWr[(long long)mode * CW * CW + e] = ar[q];
+    gWi[(long long)mode * CW * CW + e] = ai[q];
+  }
+}
+
+// Adam with bias correction on the FP32 master weights
+__global__ void adam_kernel(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  th[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// W (32x32, [i][o]) -> BF16 copies of W^T ([o][i], forward operand) and W ([i][o], backward)
+__global__ void pointwise_weights_kernel(const float* __restrict__ W, __nv_bfloat16* __restrict__ Wt,
+                                         __nv_bfloat16* __restrict__ Wn) {
+  const int e = threadIdx.x + blockIdx.x * blockDim.x;
+  if (e >= CW * CW) return;
+  const int i = e / CW, o = e % CW;
+  Wt[o * CW + i] = __float2bfloat16_rn(W[e]);
+  Wn[e] = __float2bfloat16_rn(W[e]);
+}
+
+// Input channels of sample b from a domain's staging (omega, v_x, v_y as doubles) and K
+template <typename T>
+__global__ void features_kernel(const double* __restrict__ real, const T* __restrict__ K, long long nn,
+                                float s0, float s1, float s2, float s3, float* __restrict__ x) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nn) return;
+  x[p * 4 + 0] = (float)real[p] * s0;
+  x[p * 4 + 1] = (float)real[nn + p] * s1;
+  x[p * 4 + 2] = (float)real[2 * nn + p] * s2;
+  x[p * 4 + 3] = (float)K[p] * s3;
+}
+
+__global__ void diff_kernel(const double* __restrict__ a, const double* __restrict__ b, long long n, float scale,
+                            float* __restrict__ out) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) out[p] = (float)(a[p] - b[p]) * scale;
+}
+
+__global__ void to_double_scaled_kernel(const float* __restrict__ src, long long n, float scale,
+                                        double* __restrict__ dst) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) dst[p] = (double)src[p] * (double)scale;
+}
+
+}  // namespace fno_dev
+
+// =======================================================================================
+// Host side
+// =======================================================================================
+using namespace fno_dev;
+
+struct ttsh_fno {
+  ttsh_fno_config cfg;
+  cudaStream_t stream;
+  int n, C, m, L, cin, Bmax;
+  long long nn, Pmax;
+  long long nparams;
+  // parameter offsets (floats) in the flat vector, same order as the host layout
+  long long off_Wp, off_bp, off_Wq, off_bq;
+  std::vector<long long> off_Wr, off_Wi, off_W, off_b;
+  float *theta = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+  __nv_bfloat16* wbf = nullptr;                 // BF16 copies: per layer Wr, Wi (spectral), Wt, Wn
+  std::vector<long long> boff_Wr, boff_Wi, boff_Wt, boff_Wn;
+  // DFT matrices
+  float *Fx = nullptr, *Gr = nullptr, *Gi = nullptr, *Gpr = nullptr, *Gpi = nullptr, *Bx = nullptr;
+  // activations
+  std::vector<float*> h, z;                     // h[0..L], z[0..L-1]
+  std::vector<__nv_bfloat16*> hb;               // hb[0..L-1]
+  std::vector<float*> Hr, Hi;                   // kept input modes per layer
+  float *Hx = nullptr, *Yr = nullptr, *Yi = nullptr, *Z = nullptr, *s = nullptr;
+  float *dh = nullptr, *dz = nullptr, *dspec = nullptr, *dout = nullptr, *yo = nullptr;
+  __nv_bfloat16* dzb = nullptr;
+  float *wpart = nullptr;
+  double* lpart = nullptr;
+  int wchunk, nwblk;
+  float in_scale[4] = {1, 1, 1, 1}, out_scale = 1;
+  long long adam_t = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+ttsh_status fno_fail(ttsh_status st, const char* msg) {
+  ttsh::set_last_error(msg);
+  return st;
+}
+
+ttsh_status fno_cuda(cudaError_t e, const char* what) {
+  ttsh::set_last_error(what, e);
+  return TTSH_E_CUDA;
+}
+
+#define FNO_CUDA(call, what)                        \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return fno_cuda(e_, what); \
+  } while (0)
+
+template <typename P>
+cudaError_t dalloc(ttsh_fno* f, P** ptr, size_t bytes) {
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e == cudaSuccess) {
+    f->allocs.push_back(p);
+    *ptr = static_cast<P*>(p);
+  }
+  return e;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014), output i of the stream from `seed`
+uint64_t sm64(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+double u01(uint64_t seed, uint64_t i) { return (double)(sm64(seed, i) >> 11) * (1.0 / 9007199254740992.0); }
+
+cudaError_t refresh_bf16(ttsh_fno* f) {
+  cudaStream_t s = f->stream;
+  const long long msz = (long long)2 * f->m * f->m * f->C * f->C;
+  for (int l = 0; l < f->L; ++l) {
+    to_bf16_kernel<<<(unsigned)((msz + 255) / 256), 256, 0, s>>>(f->theta + f->off_Wr[l], f->wbf + f->boff_Wr[l], msz);
+    to_bf16_kernel<<<(unsigned)((msz + 255) / 256), 256, 0, s>>>(f->theta + f->off_Wi[l], f->wbf + f->boff_Wi[l], msz);
+    pointwise_weights_kernel<<<(CW * CW + 255) / 256, 256, 0, s>>>(f->theta + f->off_W[l], f->wbf + f->boff_Wt[l],
+                                                                    f->wbf + f->boff_Wn[l]);
+  }
+  return cudaGetLastError();
+}
+
+// Forward pass for B samples (x: B*n*n x cin); leaves activations for backward.
+ttsh_status forward_impl(ttsh_fno* f, const float* x, int B, float* out, const float* target, double* loss) {
+  cudaStream_t s = f->stream;
+  const int n = f->n, C = f->C, m = f->m, L = f->L;
+  const long long P = (long long)B * f->nn;
+  const long long mC = (long long)m * C;
+  const int nmodes = 2 * m * m;
+  lift_kernel<<<(unsigned)((P * C + 255) / 256), 256, 0, s>>>(x, f->theta + f->off_Wp, f->theta + f->off_bp,
+                                                              f->cin, P, f->h[0], f->hb[0]);
+  for (int l = 0; l < L; ++l) {
+    const float* hl = f->h[l];
+    // row DFT: Hx[q] (2m x C) = Fx (2m x n) . h[q] (n x C), q = (b, y)
+    FNO_CUDA(sgemm(false, false, 2 * m, C, n, B * n, 1.f, f->Fx, n, 0, hl, C, (long long)n * C, 0.f, f->Hx, C,
+                   2LL * m * C, s), "row DFT");
+    // column DFT per sample: H = G X (complex), X = Hx_b viewed as n x 2mC
+    const long long sX = (long long)n * 2 * mC, sH = 2LL * m * mC;
+    FNO_CUDA(sgemm(false, false, 2 * m, (int)mC, n, B, 1.f, f->Gr, n, 0, f->Hx, 2 * mC, sX, 0.f, f->Hr[l], mC, sH, s), "col DFT");
+    FNO_CUDA(sgemm(false, false, 2 * m, (int)mC, n, B, -1.f, f->Gi, n, 0, f->Hx + mC, 2 * mC, sX, 1.f, f->Hr[l], mC, sH, s), "col DFT");
+    FNO_CUDA(sgemm(false, false, 2 * m, (int)mC, n, B, 1.f, f->Gr, n, 0, f->Hx + mC, 2 * mC, sX, 0.f, f->Hi[l], mC, sH, s), "col DFT");
+    FNO_CUDA(sgemm(false, false, 2 * m, (int)mC, n, B, 1.f, f->Gi, n, 0, f->Hx, 2 * mC, sX, 1.f, f->Hi[l], mC, sH, s), "col DFT");
+    // mode mixing
+    modemix_fwd_kernel<<<nmodes, CW, 0, s>>>(f->Hr[l], f->Hi[l], f->wbf + f->boff_Wr[l], f->wbf + f->boff_Wi[l],
+                                             nmodes, B, f->Yr, f->Yi);
+    // inverse column: Z (n x mC complex, stored as Re | Im blocks of width mC) = G' Y
+    FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, 1.f, f->Gpr, 2 * m, 0, f->Yr, mC, sH, 0.f, f->Z, 2 * mC, sX, s), "inv col");
+    FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, -1.f, f->Gpi, 2 * m, 0, f->Yi, mC, sH, 1.f, f->Z, 2 * mC, sX, s), "inv col");
+    FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, 1.f, f->Gpr, 2 * m, 0, f->Yi, mC, sH, 0.f, f->Z + mC, 2 * mC, sX, s), "inv col");
+    FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, 1.f, f->Gpi, 2 * m, 0, f->Yr, mC, sH, 1.f, f->Z + mC, 2 * mC, sX, s), "inv col");
+    // inverse row: s[q] (n x C) = Bx (n x 2m) . Z[q] (2m x C)
+    FNO_CUDA(sgemm(false, false, n, C, 2 * m, B * n, 1.f, f->Bx, 2 * m, 0, f->Z, C, 2LL * m * C, 0.f, f->s, C,
+                   (long long)n * C, s), "inv row");
+    // z = h W + b + s on the tensor cores, then GELU
+    PwArgs a;
+    a.A = f->hb[l];
+    a.Bt = f->wbf + f->boff_Wt[l];
+    a.bias = f->theta + f->off_b[l];
+    a.add = f->s;
+    a.out = f->z[l];
+    a.h = f->h[l + 1];
+    a.hb = l + 1 < L ? f->hb[l + 1] : nullptr;
+    a.P = P;
+    const unsigned nblk = (unsigned)((P / 16 + 7) / 8);
+    if (l + 1 < L) pointwise_mma_kernel<EPI_FWD><<<nblk, 256, 0, s>>>(a);
+    else pointwise_mma_kernel<EPI_FWD_LAST><<<nblk, 256, 0, s>>>(a);
+    FNO_CUDA(cudaGetLastError(), "pointwise layer");
+  }
+  const unsigned pblk = (unsigned)((P + 255) / 256);
+  project_kernel<<<pblk, 256, 0, s>>>(f->h[L], f->theta + f->off_Wq, f->theta + f->off_bq, P, out, target,
+                                      f->dout, f->dh, f->lpart);
+  FNO_CUDA(cudaGetLastError(), "projection");
+  if (target && loss) {
+    std::vector<double> lp(pblk);
+    FNO_CUDA(cudaMemcpyAsync(lp.data(), f->lpart, pblk * sizeof(double), cudaMemcpyDeviceToHost, s), "loss");
+    FNO_CUDA(cudaStreamSynchronize(s), "loss");
+    double acc = 0;
+    for (double v : lp) acc += v;
+    *loss = acc / (double)P;
+  }
+  return TTSH_OK;
+}
+
+ttsh_status wgrad(ttsh_fno* f, const float* A, int ca, const float* D, int cd, long long P, float* gw, float* gb) {
+  const int nout = ca * cd + cd;
+  const long long chunk = (P + f->nwblk - 1) / f->nwblk;
+  const int nblk = (int)((P + chunk - 1) / chunk);
+  wgrad_partial_kernel<<<nblk, 256, 0, f->stream>>>(A, ca, D, cd, P, (int)chunk, f->wpart);
+  wgrad_reduce_kernel<<<(nout + 255) / 256, 256, 0, f->stream>>>(f->wpart, nblk, ca, cd, gw, gb);
+  FNO_CUDA(cudaGetLastError(), "weight gradient");
+  return TTSH_OK;
+}
+
+ttsh_status backward_impl(ttsh_fno* f, const float* x, int B, const float* out) {
+  cudaStream_t s = f->stream;
+  const int n = f->n, C = f->C, m = f->m, L = f->L;
+  const long long P = (long long)B * f->nn;
+  const long long mC = (long long)m * C;
+  const long long sX = (long long)n * 2 * mC, sH = 2LL * m * mC;
+  const int nmodes = 2 * m * m;
+  (void)out;
+  ttsh_status st;
+  // projection: dWq = h_L^T dout, dbq = sum dout; dh (= dout Wq) was written by project_kernel
+  if ((st = wgrad(f, f->h[L], C, f->dout, 1, P, f->grad + f->off_Wq, f->grad + f->off_bq)) != TTSH_OK) return st;
+  for (int l = L - 1; l >= 0; --l) {
+    const long long tot = P * C;
+    gelu_bwd_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(f->dh, f->z[l], tot, l + 1 < L ? 1 : 0, f->dz, f->dzb);
+    FNO_CUDA(cudaGetLastError(), "gelu backward");
+    if ((st = wgrad(f, f->h[l], C, f->dz, C, P, f->grad + f->off_W[l], f->grad + f->off_b[l])) != TTSH_OK) return st;
+    // spectral adjoint: dZ[q] = Bx^T dz[q]
+    FNO_CUDA(sgemm(true, false, 2 * m, C, n, B * n, 1.f, f->Bx, 2 * m, 0, f->dz, C, (long long)n * C, 0.f, f->Z, C,
+                   2LL * m * C, s), "inv row adjoint");
+    // dY = G'^H dZ
+    FNO_CUDA(sgemm(true, false, 2 * m, (int)mC, n, B, 1.f, f->Gpr, 2 * m, 0, f->Z, 2 * mC, sX, 0.f, f->Yr, mC, sH, s), "inv col adjoint");
+    FNO_CUDA(sgemm(true, false, 2 * m, (int)mC, n, B, 1.f, f->Gpi, 2 * m, 0, f->Z + mC, 2 * mC, sX, 1.f, f->Yr, mC, sH, s), "inv col adjoint");
+    FNO_CUDA(sgemm(true, false, 2 * m, (int)mC, n, B, 1.f, f->Gpr, 2 * m, 0, f->Z + mC, 2 * mC, sX, 0.f, f->Yi, mC, sH, s), "inv col adjoint");
+    FNO_CUDA(sgemm(true, false, 2 * m, (int)mC, n, B, -1.f, f->Gpi, 2 * m, 0, f->Z, 2 * mC, sX, 1.f, f->Yi, mC, sH, s), "inv col adjoint");
+    // mode mixing adjoint (dH into Hx-sized scratch halves) and spectral weight gradients
+    float* dHr = f->s;                         // reuse: 2*m*mC*B floats each
+    float* dHi = f->s + (long long)B * sH;
+    modemix_bwd_kernel<<<nmodes, 256, 0, s>>>(f->Hr[l], f->Hi[l], f->Yr, f->Yi, f->wbf + f->boff_Wr[l],
+                                              f->wbf + f->boff_Wi[l], nmodes, B, dHr, dHi, f->grad + f->off_Wr[l],
+                                              f->grad + f->off_Wi[l]);
+    FNO_CUDA(cudaGetLastError(), "mode mixing adjoint");
+    // dX = G^H dH (written as Re | Im blocks into Hx)
+    FNO_CUDA(sgemm(true, false, n, (int)mC, 2 * m, B, 1.f, f->Gr, n, 0, dHr, mC, sH, 0.f, f->Hx, 2 * mC, sX, s), "col adjoint");
+    FNO_CUDA(sgemm(true, false, n, (int)mC, 2 * m, B, 1.f, f->Gi, n, 0, dHi, mC, sH, 1.f, f->Hx, 2 * mC, sX, s), "col adjoint");
+    FNO_CUDA(sgemm(true, false, n, (int)mC, 2 * m, B, 1.f, f->Gr, n, 0, dHi, mC, sH, 0.f, f->Hx + mC, 2 * mC, sX, s), "col adjoint");
+    FNO_CUDA(sgemm(true, false, n, (int)mC, 2 * m, B, -1.f, f->Gi, n, 0, dHr, mC, sH, 1.f, f->Hx + mC, 2 * mC, sX, s), "col adjoint");
+    // dh_spec[q] = Fx^T dHx[q]
+    FNO_CUDA(sgemm(true, false, n, C, 2 * m, B * n, 1.f, f->Fx, n, 0, f->Hx, C, 2LL * m * C, 0.f, f->dspec, C,
+                   (long long)n * C, s), "row adjoint");
+    // dh_l = dz W^T + dh_spec on the tensor cores
+    PwArgs a;
+    a.A = f->dzb;
+    a.Bt = f->wbf + f->boff_Wn[l];
+    a.bias = nullptr;
+    a.add = f->dspec;
+    a.out = f->dh;
+    a.h = nullptr;
+    a.hb = nullptr;
+    a.P = P;
+    pointwise_mma_kernel<EPI_BWD><<<(unsigned)((P / 16 + 7) / 8), 256, 0, s>>>(a);
+    FNO_CUDA(cudaGetLastError(), "pointwise adjoint");
+  }
+  // lift: dWp = x^T dh0, dbp = sum dh0
+  return wgrad(f, x, f->cin, f->dh, C, P, f->grad + f->off_Wp, f->grad + f->off_bp);
+}
+
+}  // namespace
+
+extern "C" {
+
+ttsh_status ttsh_fno_create(const ttsh_fno_config* cfg, uint64_t seed, void* stream, ttsh_fno** out) {
+  if (!out || !cfg) return fno_fail(TTSH_E_INVALID, "NULL argument");
+  *out = nullptr;
+  if (cfg->width != CW) return fno_fail(TTSH_E_UNSUPPORTED, "width must be 32");
+  if (cfg->in_channels != 4) return fno_fail(TTSH_E_UNSUPPORTED, "in_channels must be 4");
+  if (cfg->n < 16 || (cfg->n & (cfg->n - 1)) || cfg->n > 1024) return fno_fail(TTSH_E_INVALID, "n must be a power of two in [16, 1024]");
+  if (cfg->modes < 1 || 2 * cfg->modes > cfg->n / 2) return fno_fail(TTSH_E_INVALID, "modes must be in [1, n/4]");
+  if (cfg->layers < 1 || cfg->layers > 16 || cfg->max_batch < 1 || cfg->max_batch > 64)
+    return fno_fail(TTSH_E_INVALID, "layers in [1, 16], max_batch in [1, 64]");
+  ttsh_fno* f = new ttsh_fno();
+  f->cfg = *cfg;
+  f->stream = static_cast<cudaStream_t>(stream);
+  f->n = cfg->n;
+  f->C = cfg->width;
+  f->m = cfg->modes;
+  f->L = cfg->layers;
+  f->cin = cfg->in_channels;
+  f->Bmax = cfg->max_batch;
+  f->nn = (long long)f->n * f->n;
+  f->Pmax = f->nn * f->Bmax;
+  const int C = f->C, m = f->m, L = f->L, n = f->n;
+  const long long msz = 2LL * m * m * C * C;
+  long long o = 0;
+  f->off_Wp = o; o += (long long)f->cin * C;
+  f->off_bp = o; o += C;
+  for (int l = 0; l < L; ++l) {
+    f->off_Wr.push_back(o); o += msz;
+    f->off_Wi.push_back(o); o += msz;
+    f->off_W.push_back(o); o += C * C;
+    f->off_b.push_back(o); o += C;
+  }
+  f->off_Wq = o; o += C;
+  f->off_bq = o; o += 1;
+  f->nparams = o;
+  long long bo = 0;
+  for (int l = 0; l < L; ++l) {
+    f->boff_Wr.push_back(bo); bo += msz;
+    f->boff_Wi.push_back(bo); bo += msz;
+    f->boff_Wt.push_back(bo); bo += C * C;
+    f->boff_Wn.push_back(bo); bo += C * C;
+  }
+  auto cleanup = [&](ttsh_status st) {
+    ttsh_fno_destroy(f);
+    return st;
+  };
+  cudaError_t e = cudaSuccess;
+  const long long P = f->Pmax, PC = P * C;
+  const long long sH = 2LL * m * m * C;   // floats per sample of kept modes
+  f->nwblk = 512;
+  auto A = [&](auto** p, size_t bytes) {
+    if (e == cudaSuccess) e = dalloc(f, p, bytes);
+  };
+  A(&f->theta, f->nparams * 4);
+  A(&f->grad, f->nparams * 4);
+  A(&f->adam_m, f->nparams * 4);
+  A(&f->adam_v, f->nparams * 4);
+  A(&f->wbf, bo * 2);
+  A(&f->Fx, 2LL * m * n * 4);
+  A(&f->Gr, 2LL * m * n * 4);
+  A(&f->Gi, 2LL * m * n * 4);
+  A(&f->Gpr, 2LL * m * n * 4);
+  A(&f->Gpi, 2LL * m * n * 4);
+  A(&f->Bx, 2LL * m * n * 4);
+  f->h.assign(L + 1, nullptr);
+  f->z.assign(L, nullptr);
+  f->hb.assign(L, nullptr);
+  f->Hr.assign(L, nullptr);
+  f->Hi.assign(L, nullptr);
+  for (int l = 0; l <= L; ++l) A(&f->h[l], PC * 4);
+  for (int l = 0; l < L; ++l) {
+    A(&f->z[l], PC * 4);
+    A(&f->hb[l], PC * 2);
+    A(&f->Hr[l], f->Bmax * sH * 4);
+    A(&f->Hi[l], f->Bmax * sH * 4);
+  }
+  A(&f->Hx, (long long)f->Bmax * n * 2 * m * C * 4);
+  A(&f->Yr, f->Bmax * sH * 4);
+  A(&f->Yi, f->Bmax * sH * 4);
+  A(&f->Z, (long long)f->Bmax * n * 2 * m * C * 4);
+  A(&f->s, (PC > 2 * f->Bmax * sH ? PC : 2 * f->Bmax * sH) * 4);
+  A(&f->dh, PC * 4);
+  A(&f->dz, PC * 4);
+  A(&f->dzb, PC * 2);
+  A(&f->dspec, PC * 4);
+  A(&f->dout, P * 4);
+  A(&f->yo, P * 4);
+  A(&f->wpart, (long long)f->nwblk * (C * C + C) * 4);
+  A(&f->lpart, ((P + 255) / 256) * 8);
+  if (e != cudaSuccess) return cleanup(fno_cuda(e, "FNO allocation"));
+  // DFT matrices on the kept modes
+  {
+    const double tp = 6.283185307179586476925286766559;
+    std::vector<float> Fx(2 * m * n), Gr(2 * m * n), Gi(2 * m * n), Gpr(2 * m * n), Gpi(2 * m * n), Bx(2 * m * n);
+    const double inv = 1.0 / ((double)n * n);
+    for (int k = 0; k < m; ++k)
+      for (int x = 0; x < n; ++x) {
+        const double a = tp * (double)((long long)k * x % n) / n;
+        Fx[k * n + x] = (float)cos(a);
+        Fx[(m + k) * n + x] = (float)(-sin(a));
+        const double c = k == 0 ? 1.0 : 2.0;
+        Bx[x * 2 * m + k] = (float)(c * cos(a) * inv);
+        Bx[x * 2 * m + m + k] = (float)(-c * sin(a) * inv);
+      }
+    for (int j = 0; j < 2 * m; ++j) {
+      const int ky = j < m ? j : n - 2 * m + j;
+      for (int y = 0; y < n; ++y) {
+        const double a = tp * (double)((long long)ky * y % n) / n;
+        Gr[j * n + y] = (float)cos(a);
+        Gi[j * n + y] = (float)(-sin(a));
+        Gpr[y * 2 * m + j] = (float)cos(a);
+        Gpi[y * 2 * m + j] = (float)sin(a);
+      }
+    }
+    const std::vector<float>* src[6] = {&Fx, &Gr, &Gi, &Gpr, &Gpi, &Bx};
+    float* dst[6] = {f->Fx, f->Gr, f->Gi, f->Gpr, f->Gpi, f->Bx};
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i)
+      e = cudaMemcpy(dst[i], src[i]->data(), src[i]->size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cleanup(fno_cuda(e, "DFT matrices"));
+  }
+  // seeded initialisation: pointwise weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)), biases 0,
+  // spectral weights U(0, 1/(C*C)) (real and imaginary parts)
+  {
+    std::vector<float> th(f->nparams, 0.f);
+    uint64_t ctr = 0;
+    auto uni = [&](long long off, long long cnt, double lo, double hi) {
+      for (long long i = 0; i < cnt; ++i) th[off + i] = (float)(lo + (hi - lo) * u01(seed, ctr++));
+    };
+    uni(f->off_Wp, (long long)f->cin * C, -1.0 / sqrt((double)f->cin), 1.0 / sqrt((double)f->cin));
+    for (int l = 0; l < L; ++l) {
+      uni(f->off_Wr[l], msz, 0.0, 1.0 / (C * C));
+      uni(f->off_Wi[l], msz, 0.0, 1.0 / (C * C));
+      uni(f->off_W[l], (long long)C * C, -1.0 / sqrt((double)C), 1.0 / sqrt((double)C));
+    }
+    uni(f->off_Wq, C, -1.0 / sqrt((double)C), 1.0 / sqrt((double)C));
+    e = cudaMemcpy(f->theta, th.data(), th.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(f->adam_m, 0, f->nparams * 4);
+    if (e == cudaSuccess) e = cudaMemset(f->adam_v, 0, f->nparams * 4);
+    if (e == cudaSuccess) e = cudaMemset(f->grad, 0, f->nparams * 4);
+    if (e == cudaSuccess) e = refresh_bf16(f);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    if (e != cudaSuccess) return cleanup(fno_cuda(e, "FNO initialisation"));
+  }
+  *out = f;
+  return TTSH_OK;
+}
+
+void ttsh_fno_destroy(ttsh_fno* f) {
+  if (!f) return;
+  for (void* p : f->allocs) cudaFree(p);
+  delete f;
+}
+
+int64_t ttsh_fno_num_params(const ttsh_fno* f) { return f ? f->nparams : -1; }
+
+ttsh_status ttsh_fno_get_params(ttsh_fno* f, float* host) {
+  if (!f || !host) return fno_fail(TTSH_E_INVALID, "NULL argument");
+  FNO_CUDA(cudaMemcpyAsync(host, f->theta, f->nparams * 4, cudaMemcpyDeviceToHost, f->stream), "get params");
+  FNO_CUDA(cudaStreamSynchronize(f->stream), "get params");
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_fno_set_params(ttsh_fno* f, const float* host) {
+  if (!f || !host) return fno_fail(TTSH_E_INVALID, "NULL argument");
+  FNO_CUDA(cudaMemcpyAsync(f->theta, host, f->nparams * 4, cudaMemcpyHostToDevice, f->stream), "set params");
+  FNO_CUDA(refresh_bf16(f), "set params");
+  FNO_CUDA(cudaStreamSynchronize(f->stream), "set params");
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_fno_set_scales(ttsh_fno* f, const float* in_scale, float out_scale) {
+  if (!f || !in_scale || !(out_scale != 0.f)) return fno_fail(TTSH_E_INVALID, "bad scales");
+  for (int i = 0; i < 4; ++i) f->in_scale[i] = in_scale[i];
+  f->out_scale = out_scale;
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_fno_forward(ttsh_fno* f, const float* x, float* y, int32_t batch) {
+  if (!f || !x || !y) return fno_fail(TTSH_E_INVALID, "NULL argument");
+  if (batch < 1 || batch > f->Bmax) return fno_fail(TTSH_E_INVALID, "batch out of range");
+  return forward_impl(f, x, batch, y, nullptr, nullptr);
+}
+
+ttsh_status ttsh_fno_loss_grad(ttsh_fno* f, const float* x, const float* target, int32_t batch, double* loss,
+                               float* grad_host) {
+  if (!f || !x || !target) return fno_fail(TTSH_E_INVALID, "NULL argument");
+  if (batch < 1 || batch > f->Bmax) return fno_fail(TTSH_E_INVALID, "batch out of range");
+  double l = 0;
+  ttsh_status st = forward_impl(f, x, batch, f->yo, target, &l);
+  if (st != TTSH_OK) return st;
+  if ((st = backward_impl(f, x, batch, nullptr)) != TTSH_OK) return st;
+  if (grad_host) {
+    FNO_CUDA(cudaMemcpyAsync(grad_host, f->grad, f->nparams * 4, cudaMemcpyDeviceToHost, f->stream), "get grad");
+  }
+  FNO_CUDA(cudaStreamSynchronize(f->stream), "loss_grad");
+  if (loss) *loss = l;
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_fno_adam_step(ttsh_fno* f, float lr, float beta1, float beta2, float eps) {
+  if (!f || !(lr > 0)) return fno_fail(TTSH_E_INVALID, "bad arguments");
+  f->adam_t += 1;
+  const float c1 = 1.f - powf(beta1, (float)f->adam_t), c2 = 1.f - powf(beta2, (float)f->adam_t);
+  adam_kernel<<<(unsigned)((f->nparams + 255) / 256), 256, 0, f->stream>>>(f->theta, f->grad, f->adam_m, f->adam_v,
+                                                                           f->nparams, lr, beta1, beta2, eps, c1, c2);
+  FNO_CUDA(cudaGetLastError(), "adam");
+  FNO_CUDA(refresh_bf16(f), "adam");
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_fno_features(ttsh_fno* f, ttsh_domain* d, float* x, int32_t sample) {
+  if (!f || !d || !x) return fno_fail(TTSH_E_INVALID, "NULL argument");
+  if (ttsh::domain_n(d) != f->n) return fno_fail(TTSH_E_INVALID, "domain grid differs from the network's");
+  if (sample < 0 || sample >= f->Bmax) return fno_fail(TTSH_E_INVALID, "sample out of range");
+  ttsh_status st = (ttsh_status)ttsh::domain_fields_to_staging(d);
+  if (st != TTSH_OK) return st;
+  cudaStream_t s = ttsh::domain_stream(d);
+  const ttsh::DomainDev* dv = ttsh::domain_dev(d);
+  float* xs = x + (long long)sample * f->nn * 4;
+  const unsigned blk = (unsigned)((f->nn + 255) / 256);
+  if (ttsh::domain_precision(d) == 32)
+    features_kernel<float><<<blk, 256, 0, s>>>(dv->real, (const float*)dv->K, f->nn, f->in_scale[0], f->in_scale[1],
+                                                f->in_scale[2], f->in_scale[3], xs);
+  else
+    features_kernel<double><<<blk, 256, 0, s>>>(dv->real, (const double*)dv->K, f->nn, f->in_scale[0],
+                                                 f->in_scale[1], f->in_scale[2], f->in_scale[3], xs);
+  FNO_CUDA(cudaGetLastError(), "features");
+  FNO_CUDA(cudaStreamSynchronize(s), "features");
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_fno_residual(ttsh_fno* f, ttsh_domain* truth, ttsh_domain* base, float* target, int32_t sample) {
+  if (!f || !truth || !base || !target) return fno_fail(TTSH_E_INVALID, "NULL argument");
+  if (ttsh::domain_n(truth) != f->n || ttsh::domain_n(base) != f->n)
+    return fno_fail(TTSH_E_INVALID, "domain grid differs from the network's");
+  if (sample < 0 || sample >= f->Bmax) return fno_fail(TTSH_E_INVALID, "sample out of range");
+  ttsh_status st = (ttsh_status)ttsh::domain_fields_to_staging(truth);
+  if (st != TTSH_OK) return st;
+  st = (ttsh_status)ttsh::domain_fields_to_staging(base);
+  if (st != TTSH_OK) return st;
+  FNO_CUDA(cudaStreamSynchronize(ttsh::domain_stream(truth)), "residual");
+  cudaStream_t s = ttsh::domain_stream(base);
+  diff_kernel<<<(unsigned)((f->nn + 255) / 256), 256, 0, s>>>(ttsh::domain_dev(truth)->real,
+                                                                ttsh::domain_dev(base)->real, f->nn, f->out_scale,
+                                                                target + (long long)sample * f->nn);
+  FNO_CUDA(cudaGetLastError(), "residual");
+  FNO_CUDA(cudaStreamSynchronize(s), "residual");
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_fno_correct(ttsh_fno* f, ttsh_domain* d, float* scratch) {
+  if (!f || !d || !scratch) return fno_fail(TTSH_E_INVALID, "NULL argument");
+  ttsh_status st = ttsh_fno_features(f, d, scratch, 0);
+  if (st != TTSH_OK) return st;
+  float* y = scratch + f->nn * 4;
+  cudaStream_t keep = f->stream;
+  f->stream = ttsh::domain_stream(d);
+  st = forward_impl(f, scratch, 1, y, nullptr, nullptr);
+  f->stream = keep;
+  if (st != TTSH_OK) return st;
+  const ttsh::DomainDev* dv = ttsh::domain_dev(d);
+  to_double_scaled_kernel<<<(unsigned)((f->nn + 255) / 256), 256, 0, ttsh::domain_stream(d)>>>(
+      y, f->nn, 1.f / f->out_scale, dv->real);
+  FNO_CUDA(cudaGetLastError(), "correction");
+  return (ttsh_status)ttsh::domain_add_vorticity_from_staging(d);
+}
+
+}  // extern "C"

@@ -49,7 +49,7 @@ struct Args {
 
 enum RowKind { ROW_STEP = 0, ROW_FWD_VEL = 1, ROW_FWD_MASK = 2, ROW_INV_FIELDS = 3,
                ROW_INV_MASK = 4, ROW_INV_DIAG = 5 };
-enum ColMode { COL_STEP = 0, COL_PROLOGUE = 1, COL_PROJECT = 2, COL_MASK = 3 };
+enum ColMode { COL_STEP = 0, COL_PROLOGUE = 1, COL_PROJECT = 2, COL_MASK = 3, COL_ADDW = 4 };
 
 constexpr int kDiagQ = 5;   // per-block partials: sum|v|^2, sum w^2, sum|e_th.v|, sum|v|, #nonfinite
 constexpr int kSmemLimit = 220 * 1024;
@@ -114,12 +114,12 @@ struct ColGeo {
   static constexpr int PS = ilog2(PE);
   static constexpr int LP = padded_len<N, PS>();
   static constexpr int TT = N / PE;
-  static constexpr int NF = MODE == COL_STEP ? 3 : MODE == COL_PROJECT ? 2 : MODE == COL_MASK ? 1 : 0;
+  static constexpr int NF = MODE == COL_STEP ? 3 : MODE == COL_PROJECT ? 2 : (MODE == COL_MASK || MODE == COL_ADDW) ? 1 : 0;
   static constexpr int NI = MODE == COL_MASK ? 1 : 4;
   static constexpr int CB = (int)sizeof(cplx<T>);
   static constexpr int TW_BYTES = align16(TwTab<T, N>::ENTRIES * CB);
   static constexpr int ACC_BYTES = align16(NK * CB);
-  static constexpr int WS_BYTES = MODE == COL_STEP ? align16(NK * CB) : 0;
+  static constexpr int WS_BYTES = (MODE == COL_STEP || MODE == COL_ADDW) ? align16(NK * CB) : 0;
   static constexpr int FIXED = TW_BYTES + ACC_BYTES + WS_BYTES + 64;
   static constexpr int FB0 = cmax(NF, NI) >= 4 ? 4 : cmax(NF, NI);
   static constexpr int FB = (FIXED + FB0 * LP * CB <= kSmemLimit) ? FB0
@@ -331,7 +331,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
   // ---- forward column transforms and curl assembly ----
   if constexpr (MODE != COL_PROLOGUE) {
     constexpr int NF = Geo::NF;
-    if constexpr (MODE == COL_STEP) {
+    if constexpr (MODE == COL_STEP || MODE == COL_ADDW) {
       for (int j = tid; j < NK; j += NT) cp_async<CB>(ws + j, A.what + (size_t)kx * NK + j);
     }
     for (int f0 = 0; f0 < NF; f0 += FB) {
@@ -347,7 +347,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
         for (int b = 0; b < nb; ++b) {
           const int f = f0 + b;
           const cplx<T> v = buf[b * LP + padi<PS>(idx)];
-          if constexpr (MODE == COL_MASK) {
+          if constexpr (MODE == COL_MASK || MODE == COL_ADDW) {
             a = v;
           } else {
             // f = 0: (rhs1_x | v_x) -> -i ky; f = 1: (rhs1_y | v_y) -> +i kx; f = 2: rhs2 -> 1
@@ -378,6 +378,10 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
       } else if constexpr (MODE == COL_PROJECT) {
         wn = acc[j] * invN;
         if (m2 == 0 || m2 > M * M) wn = mk<T>(0, 0);
+      } else if constexpr (MODE == COL_ADDW) {
+        // correction delta^ = DFT[delta omega] on the 1/2-rule disc, delta^(0) = 0
+        wn = acc[j] * invN;
+        if (m2 == 0 || m2 > M * M) wn = mk<T>(0, 0);
       } else {   // COL_MASK: keep |m|^2 <= (N/8)^2, fold both 1/N factors of the round trip
         wn = acc[j] * (invN * invN);
         if (m2 > (N / 8) * (N / 8)) wn = mk<T>(0, 0);
@@ -398,7 +402,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
       }
     }
     __syncthreads();
-    if constexpr (MODE == COL_STEP || MODE == COL_PROJECT) {
+    if constexpr (MODE == COL_STEP || MODE == COL_PROJECT || MODE == COL_ADDW) {
       // line 13: Hermitian average; with half-spectrum storage only mx = 0 pairs are stored
       if (kx == 0) {
         for (int ky = 1 + tid; ky <= M; ky += NT) {
@@ -406,6 +410,14 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
           const cplx<T> h = (p + conjg(q)) * (T)0.5;
           acc[ky] = h;
           acc[NK - ky] = conjg(h);
+        }
+        __syncthreads();
+      }
+      if constexpr (MODE == COL_ADDW) {
+        for (int j = tid; j < NK; j += NT) acc[j] = acc[j] + ws[j];
+        if (kx == 0 && tid == 0) {
+          s0[2] = A.vmean[0];
+          s0[3] = A.vmean[1];
         }
         __syncthreads();
       }

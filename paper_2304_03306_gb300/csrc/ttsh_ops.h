@@ -27,7 +27,7 @@ struct DomainDev {
 
 enum { K_ROW_STEP = 0, K_ROW_FWD_VEL = 1, K_ROW_FWD_MASK = 2, K_ROW_INV_FIELDS = 3,
        K_ROW_INV_MASK = 4, K_ROW_INV_DIAG = 5 };
-enum { K_COL_STEP = 0, K_COL_PROLOGUE = 1, K_COL_PROJECT = 2, K_COL_MASK = 3 };
+enum { K_COL_STEP = 0, K_COL_PROLOGUE = 1, K_COL_PROJECT = 2, K_COL_MASK = 3, K_COL_ADDW = 4 };
 
 using RowFn = cudaError_t (*)(int kind, const DomainDev&, cudaStream_t);
 using ColFn = cudaError_t (*)(int mode, const DomainDev&, cudaStream_t);
@@ -75,6 +75,22 @@ bool ops_f64_large(int n, SizeOps* o);
 // outside ttsh_api.cu).
 void set_last_error(const char* msg);
 void set_last_error(const char* what, cudaError_t e);
+
+}  // namespace ttsh
+
+struct ttsh_domain;
+namespace ttsh {
+// Accessors used by the corrector (ttsh_fno.cu) to work on a domain's device state.
+const DomainDev* domain_dev(const ttsh_domain* d);
+cudaStream_t domain_stream(const ttsh_domain* d);
+int domain_precision(const ttsh_domain* d);
+int domain_n(const ttsh_domain* d);
+double domain_dx(const ttsh_domain* d);
+// Real-space omega, v_x, v_y of the state into the domain's double staging planes 0..2.
+int domain_fields_to_staging(ttsh_domain* d);
+// Add the real field in staging plane 0 to omega (projected onto the 1/2-rule disc,
+// Hermitian, zero mean) and refresh the inter-pass buffers.
+int domain_add_vorticity_from_staging(ttsh_domain* d);
 
 cudaError_t launch_diag_reduce(const double* part, int nblocks, double* out, cudaStream_t s);
 cudaError_t launch_spectrum_reduce(const double* colhist, int ncols, int nbins, double scale,

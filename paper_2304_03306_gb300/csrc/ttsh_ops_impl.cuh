@@ -91,6 +91,7 @@ static cudaError_t launch_col(int mode, const DomainDev& d, cudaStream_t s) {
     case K_COL_PROLOGUE: return launch_col_mode<T, N, COL_PROLOGUE>(d, s);
     case K_COL_PROJECT: return launch_col_mode<T, N, COL_PROJECT>(d, s);
     case K_COL_MASK: return launch_col_mode<T, N, COL_MASK>(d, s);
+    case K_COL_ADDW: return launch_col_mode<T, N, COL_ADDW>(d, s);
   }
   return cudaErrorInvalidValue;
 }

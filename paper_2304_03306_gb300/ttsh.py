@@ -42,6 +42,11 @@ class ttsh_diag(ctypes.Structure):
                 ("nonfinite", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class ttsh_fno_config(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("width", ctypes.c_int32), ("modes", ctypes.c_int32),
+                ("layers", ctypes.c_int32), ("in_channels", ctypes.c_int32), ("max_batch", ctypes.c_int32)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
@@ -80,6 +85,20 @@ def load_library(path: str = LIB_PATH):
         "ttsh_batch_synchronize": (ctypes.c_int, [_P]),
         "ttsh_batch_groups": (ctypes.c_int32, [_P]),
         "ttsh_batch_destroy": (None, [_P]),
+        "ttsh_restrict": (ctypes.c_int, [_P, _P]),
+        "ttsh_fno_create": (ctypes.c_int, [ctypes.POINTER(ttsh_fno_config), ctypes.c_uint64, _P, ctypes.POINTER(_P)]),
+        "ttsh_fno_destroy": (None, [_P]),
+        "ttsh_fno_num_params": (ctypes.c_int64, [_P]),
+        "ttsh_fno_get_params": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
+        "ttsh_fno_set_params": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
+        "ttsh_fno_set_scales": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_float]),
+        "ttsh_fno_forward": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
+        "ttsh_fno_loss_grad": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_float)]),
+        "ttsh_fno_adam_step": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+        "ttsh_fno_features": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
+        "ttsh_fno_residual": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32]),
+        "ttsh_fno_correct": (ctypes.c_int, [_P, _P, _P]),
         "ttsh_step_count": (ctypes.c_int64, [_P]),
         "ttsh_step_noalloc": (ctypes.c_int, [ctypes.POINTER(ttsh_params), _P, _P, _P, ctypes.c_int64, _P]),
         "ttsh_last_error": (ctypes.c_char_p, []),
@@ -277,6 +296,74 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def ttsh_restrict(fine, coarse):
+    _check(load_library().ttsh_restrict(fine, coarse))
+
+
+_FP = ctypes.POINTER(ctypes.c_float)
+
+
+class FNO:
+    """Learned corrector (Fourier neural operator) run by the library's kernels.
+
+    Device arrays are passed as integer pointers (e.g. torch tensor .data_ptr())."""
+
+    def __init__(self, n=256, width=32, modes=16, layers=4, max_batch=8, seed=0, stream: int | None = None):
+        self.cfg = ttsh_fno_config(n, width, modes, layers, 4, max_batch)
+        self.n = n
+        self.h = _P()
+        lib = load_library()
+        _check(lib.ttsh_fno_create(ctypes.byref(self.cfg), int(seed), stream, ctypes.byref(self.h)))
+        self.nparams = int(lib.ttsh_fno_num_params(self.h))
+
+    def close(self):
+        if self.h:
+            load_library().ttsh_fno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.nparams, dtype=np.float32)
+        _check(load_library().ttsh_fno_get_params(self.h, out.ctypes.data_as(_FP)))
+        return out
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        assert a.size == self.nparams
+        _check(load_library().ttsh_fno_set_params(self.h, a.ctypes.data_as(_FP)))
+
+    def set_scales(self, in_scale, out_scale: float):
+        a = np.ascontiguousarray(in_scale, dtype=np.float32)
+        _check(load_library().ttsh_fno_set_scales(self.h, a.ctypes.data_as(_FP), float(out_scale)))
+
+    def forward(self, x_ptr: int, y_ptr: int, batch: int):
+        _check(load_library().ttsh_fno_forward(self.h, x_ptr, y_ptr, int(batch)))
+
+    def loss_grad(self, x_ptr: int, t_ptr: int, batch: int, want_grad: bool = False):
+        loss = ctypes.c_double()
+        g = np.empty(self.nparams, dtype=np.float32) if want_grad else None
+        _check(load_library().ttsh_fno_loss_grad(self.h, x_ptr, t_ptr, int(batch), ctypes.byref(loss),
+                                                 g.ctypes.data_as(_FP) if want_grad else None))
+        return loss.value, g
+
+    def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        _check(load_library().ttsh_fno_adam_step(self.h, lr, beta1, beta2, eps))
+
+    def features(self, dom, x_ptr: int, sample: int = 0):
+        _check(load_library().ttsh_fno_features(self.h, dom.h, x_ptr, int(sample)))
+
+    def residual(self, truth, base, t_ptr: int, sample: int = 0):
+        _check(load_library().ttsh_fno_residual(self.h, truth.h, base.h, t_ptr, int(sample)))
+
+    def correct(self, dom, scratch_ptr: int):
+        _check(load_library().ttsh_fno_correct(self.h, dom.h, scratch_ptr))
 
 
 def ttsh_synchronize(h):
