@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     return ap.parse_args()
 
 
@@ -286,6 +287,34 @@ def run_ours(args, rank, world, local_rank):
         for o in objs:
             o.close()
 
+    # ---- learned corrector: train on solver-generated data, evaluate on a held-out radius ----
+    surrogate = None
+    if not args.no_surrogate and rank == 0:
+        from paper_2304_03306_gb300 import corrector as Cr
+        t0 = time.perf_counter()
+        net = ttsh.FNO(n=256, width=32, modes=16, layers=4, max_batch=8, seed=0)
+        X, Y = Cr.generate(net, ntraj=48, samples=16, spacing=40, transient=3000, amplitude=0.3, seed=0)
+        Cr.normalise(net, X, Y)
+        t_gen = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        losses = Cr.train(net, X, Y, iters=600, batch=8, lr=1e-3, log_every=599)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        del X, Y
+        ev = Cr.evaluate(net, 6.3, coarse_steps=1000, sample_every=50, correct_every=1)
+        net.close()
+        surrogate = {
+            "metric": "wall-clock speedup of the coarse (256^2, 4 dt) solver + FNO corrector over the fine "
+                      "FP32 512^2 solver for the same physical time, and time-averaged E(k) error (s <= 64)",
+            "speedup": ev["speedup_fno"], "spectrum_error": ev["spectrum_error_fno"],
+            "spectrum_error_without_corrector": ev["spectrum_error_plain"],
+            "speedup_without_corrector": ev["speedup_plain"],
+            "psi_fine": ev["psi_fine"], "psi_fno": ev["psi_fno"], "psi_plain": ev["psi_plain"],
+            "held_out_radius": 6.3, "coarse_steps": 1000, "t_fine_s": ev["t_fine"], "t_fno_s": ev["t_fno"],
+            "train": {"trajectories": 48, "samples": 768, "iters": 600, "batch": 8,
+                      "loss_first_last": [losses[0][1], losses[-1][1]], "t_generate_s": t_gen, "t_train_s": t_train},
+            "network": "FNO 4 layers, width 32, 16 modes, BF16 weights, FP32 accumulate"}
+
     # ---- end to end through the public API with host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -348,7 +377,7 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "flushed (256 MiB write) before every timed step; the state stays L2-resident within a step",
                    "parallelism": "replicas" if world == 1 else f"independent domains x{world}"},
         "e2e": e2e, "gpu_launches": 2 * S * K, "clocks": clk, "roofline": roofline,
-        "cpu_baseline": cpu, "fp64": fp64, "batched": batched,
+        "cpu_baseline": cpu, "fp64": fp64, "batched": batched, "surrogate": surrogate,
         "diagnostics_after": {"energy": diag["energy"], "psi": diag["psi"], "nonfinite": diag["nonfinite"]},
         "ms_per_solver_step": 1e3 * t32 / (K * S),
     }

@@ -213,7 +213,8 @@ void ttsh_batch_destroy(ttsh_batch* b);           /* NULL is a no-op; domains ar
  * unitary coefficients are the fine ones times n_coarse/n_fine on the coarse 1/2-rule disc,
  * so the coarse real-space fields are the band-limited fine fields sampled on the coarse
  * grid.  Used to build the learned corrector's training targets.  Resets the coarse step
- * counter; asynchronous on the coarse domain's stream (waits for the fine stream first). */
+ * counter.  Waits for the fine domain's stream, runs on the coarse domain's stream and
+ * synchronises it before returning. */
 ttsh_status ttsh_restrict(const ttsh_domain* fine, ttsh_domain* coarse);
 
 /* ---------------------------------------------------------------------------------------
@@ -258,6 +259,11 @@ ttsh_status ttsh_fno_residual(ttsh_fno* f, ttsh_domain* truth, ttsh_domain* base
  * 1/2-rule disc (Hermitian, zero mean) as Algorithm 1's post-processing does.  scratch: a
  * device buffer of 5*n*n floats. */
 ttsh_status ttsh_fno_correct(ttsh_fno* f, ttsh_domain* d, float* scratch);
+/* Corrected rollout: nsteps solver steps of the domain with a correction after every
+ * correct_every steps (a trailing partial period is stepped without correction).  One
+ * period is recorded as a CUDA graph and replayed.  correct_every must be in [1, 64].
+ * Synchronises. */
+ttsh_status ttsh_fno_rollout(ttsh_fno* f, ttsh_domain* d, int64_t nsteps, int32_t correct_every, float* scratch);
 
 /* Block the host until the domain's stream is idle; reports deferred CUDA errors. */
 ttsh_status ttsh_synchronize(ttsh_domain* d);

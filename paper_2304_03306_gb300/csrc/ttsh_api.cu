@@ -301,6 +301,7 @@ int domain_precision(const ttsh_domain* d) { return d->p.precision; }
 int domain_n(const ttsh_domain* d) { return d->n; }
 double domain_dx(const ttsh_domain* d) { return d->p.dx; }
 int domain_fields_to_staging(ttsh_domain* d) { return run_row(d, K_ROW_INV_FIELDS, d->stream); }
+void domain_add_steps(ttsh_domain* d, int64_t n) { d->steps += n; }
 int domain_add_vorticity_from_staging(ttsh_domain* d) {
   ttsh_status st = run_row(d, K_ROW_FWD_MASK, d->stream);   // one real field forward
   if (st != TTSH_OK) return st;
@@ -883,6 +884,7 @@ ttsh_status ttsh_restrict(const ttsh_domain* fine, ttsh_domain* coarse) {
   ttsh_status st = run_col(coarse, ttsh::K_COL_PROLOGUE, coarse->stream);
   if (st != TTSH_OK) return st;
   coarse->steps = 0;
+  TTSH_CUDA(cudaStreamSynchronize(coarse->stream), "restrict");
   return TTSH_OK;
 }
 

@@ -889,8 +889,57 @@ ttsh_status ttsh_fno_features(ttsh_fno* f, ttsh_domain* d, float* x, int32_t sam
     features_kernel<double><<<blk, 256, 0, s>>>(dv->real, (const double*)dv->K, f->nn, f->in_scale[0],
                                                  f->in_scale[1], f->in_scale[2], f->in_scale[3], xs);
   FNO_CUDA(cudaGetLastError(), "features");
-  FNO_CUDA(cudaStreamSynchronize(s), "features");
   return TTSH_OK;
+}
+
+ttsh_status ttsh_fno_rollout(ttsh_fno* f, ttsh_domain* d, int64_t nsteps, int32_t correct_every, float* scratch) {
+  if (!f || !d || !scratch) return fno_fail(TTSH_E_INVALID, "NULL argument");
+  if (nsteps < 0 || correct_every < 1 || correct_every > 64)
+    return fno_fail(TTSH_E_INVALID, "nsteps >= 0 and correct_every in [1, 64] required");
+  if (ttsh::domain_n(d) != f->n) return fno_fail(TTSH_E_INVALID, "domain grid differs from the network's");
+  if (nsteps == 0) return TTSH_OK;
+  // Record one period (correct_every solver steps + one correction) as a CUDA graph on a
+  // private stream, then replay it on the domain's stream.
+  cudaStream_t user = ttsh::domain_stream(d), cap = nullptr;
+  FNO_CUDA(cudaStreamSynchronize(user), "rollout");
+  FNO_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "rollout stream");
+  const int64_t periods = nsteps / correct_every, rest = nsteps % correct_every;
+  ttsh_status st = TTSH_OK;
+  cudaGraphExec_t ge = nullptr;
+  if (periods > 0) {
+    // kernels must have their attributes set before capture: run one period eagerly
+    if ((st = ttsh_step(d, correct_every)) == TTSH_OK) st = ttsh_fno_correct(f, d, scratch);
+    if (st == TTSH_OK && periods > 1) {
+      ttsh_set_stream(d, cap);
+      cudaStream_t keep = f->stream;
+      cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        st = ttsh_step(d, correct_every);
+        if (st == TTSH_OK) st = ttsh_fno_correct(f, d, scratch);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (st == TTSH_OK && e2 == cudaSuccess) e2 = cudaGraphInstantiate(&ge, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (st == TTSH_OK && e2 != cudaSuccess) st = fno_cuda(e2, "rollout capture");
+      } else {
+        st = fno_cuda(e, "rollout capture");
+      }
+      f->stream = keep;
+      ttsh_set_stream(d, user);
+      for (int64_t i = 1; i < periods && st == TTSH_OK; ++i) {
+        cudaError_t e3 = cudaGraphLaunch(ge, user);
+        if (e3 != cudaSuccess) st = fno_cuda(e3, "rollout replay");
+      }
+      // the capture counted one period that did not run; the replays ran periods - 1
+      if (st == TTSH_OK) ttsh::domain_add_steps(d, (periods - 2) * (int64_t)correct_every);
+    }
+  }
+  if (st == TTSH_OK && rest > 0) st = ttsh_step(d, rest);
+  if (ge) cudaGraphExecDestroy(ge);
+  cudaError_t e4 = cudaStreamSynchronize(user);
+  cudaStreamDestroy(cap);
+  if (st == TTSH_OK && e4 != cudaSuccess) st = fno_cuda(e4, "rollout");
+  return st;
 }
 
 ttsh_status ttsh_fno_residual(ttsh_fno* f, ttsh_domain* truth, ttsh_domain* base, float* target, int32_t sample) {

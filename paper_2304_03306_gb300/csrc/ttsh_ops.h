@@ -91,6 +91,8 @@ int domain_fields_to_staging(ttsh_domain* d);
 // Add the real field in staging plane 0 to omega (projected onto the 1/2-rule disc,
 // Hermitian, zero mean) and refresh the inter-pass buffers.
 int domain_add_vorticity_from_staging(ttsh_domain* d);
+// Adjust the step counter (for steps replayed from a graph the domain did not record).
+void domain_add_steps(ttsh_domain* d, int64_t n);
 
 cudaError_t launch_diag_reduce(const double* part, int nblocks, double* out, cudaStream_t s);
 cudaError_t launch_spectrum_reduce(const double* colhist, int ncols, int nbins, double scale,

@@ -99,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "ttsh_fno_features": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32]),
         "ttsh_fno_residual": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32]),
         "ttsh_fno_correct": (ctypes.c_int, [_P, _P, _P]),
+        "ttsh_fno_rollout": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
         "ttsh_step_count": (ctypes.c_int64, [_P]),
         "ttsh_step_noalloc": (ctypes.c_int, [ctypes.POINTER(ttsh_params), _P, _P, _P, ctypes.c_int64, _P]),
         "ttsh_last_error": (ctypes.c_char_p, []),
@@ -364,6 +365,9 @@ class FNO:
 
     def correct(self, dom, scratch_ptr: int):
         _check(load_library().ttsh_fno_correct(self.h, dom.h, scratch_ptr))
+
+    def rollout(self, dom, nsteps: int, scratch_ptr: int, correct_every: int = 1):
+        _check(load_library().ttsh_fno_rollout(self.h, dom.h, int(nsteps), int(correct_every), scratch_ptr))
 
 
 def ttsh_synchronize(h):

@@ -173,3 +173,39 @@ def test_correct_adds_projected_network_output(T, torch):
     w_after, v_after = dom.spectral_state()
     assert np.abs(w_after - w_before).max() <= 1e-5 * max(1.0, np.abs(w_before).max())
     assert np.array_equal(v_after, v_before)
+
+
+def test_rollout_graph_equals_manual_loop(T, torch):
+    n, dx = 64, 0.32
+    mask = ti.circle_mask(n, dx, 5.4)
+    vx, vy = ti.noise_velocity(mask, 5, 0.3)
+    net, _ = make(T, seed=13, n=n, max_batch=1)
+    net.set_scales(np.array([0.5, 2.0, 2.0, 1.0], np.float32), 8.0)
+    scratch = torch.zeros(5 * n * n, device="cuda")
+    a = T.Domain(mask, n, dx, precision=32, dt=0.04)
+    b = T.Domain(mask, n, dx, precision=32, dt=0.04)
+    a.set_velocity(vx, vy)
+    b.set_velocity(vx, vy)
+    net.rollout(a, 23, scratch.data_ptr(), correct_every=2)
+    for _ in range(11):
+        b.step(2)
+        net.correct(b, scratch.data_ptr())
+    b.step(1)
+    b.synchronize()
+    assert a.steps == b.steps == 23
+    wa, va = a.spectral_state()
+    wb, vb = b.spectral_state()
+    assert np.array_equal(wa, wb) and np.array_equal(va, vb)
+
+
+def test_corrector_workflow_small(T, torch):
+    from paper_2304_03306_gb300 import corrector as Cr
+    net = T.FNO(n=256, width=32, modes=8, layers=2, max_batch=4, seed=1)
+    X, Y = Cr.generate(net, ntraj=3, samples=2, spacing=8, transient=40, amplitude=0.3, seed=2)
+    assert X.shape == (6, 256, 256, 4) and Y.shape == (6, 256, 256)
+    assert bool(torch.isfinite(X).all()) and bool(torch.isfinite(Y).all())
+    Cr.normalise(net, X, Y)
+    losses = Cr.train(net, X, Y, iters=20, batch=4, lr=1e-3, log_every=19)
+    assert losses[-1][1] < losses[0][1]
+    r = Cr.evaluate(net, 6.3, coarse_steps=40, sample_every=20, transient=40)
+    assert r["nonfinite"] == 0 and r["t_fno"] > 0 and 0 <= r["spectrum_error_plain"] < 10
