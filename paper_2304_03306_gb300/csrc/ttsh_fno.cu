@@ -314,6 +314,175 @@ __global__ void wgrad_reduce_kernel(const float* __restrict__ part, int nblk, in
   else gb[o - ca * cd] = (float)s;
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Row DFT onto the kept kx for one (sample, y) row: Hx[k][c] = sum_x F[k][x] h[x][c], with
+// F rows 0..m-1 = cos, m..2m-1 = -sin (2 pi kx x / n).  One block of 256 threads per row.
+__global__ void __launch_bounds__(256) row_dft_kernel(const float* __restrict__ h, const float* __restrict__ F,
+                                                      int n, int m, float* __restrict__ Hx) {
+  extern __shared__ __align__(16) float sm[];
+  float* hs = sm;            // [n][C]
+  float* fs = sm + n * CW;   // [2m][n]
+  const long long q = blockIdx.x;
+  const float* hq = h + q * n * CW;
+  for (int e = threadIdx.x; e < n * CW / 4; e += 256) cp_async16(hs + 4 * e, hq + 4 * e);
+  for (int e = threadIdx.x; e < 2 * m * n / 4; e += 256) cp_async16(fs + 4 * e, F + 4 * e);
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  // thread (c, g) computes kx rows k = g, g + 8, ...; four x at a time from float4 loads
+  const int c = threadIdx.x % CW, g = threadIdx.x / CW;
+  for (int k0 = g; k0 < 2 * m; k0 += 32) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int x = 0; x < n; x += 4) {
+      const float h0 = hs[x * CW + c], h1 = hs[(x + 1) * CW + c], h2 = hs[(x + 2) * CW + c], h3 = hs[(x + 3) * CW + c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int k = k0 + 8 * r;
+        if (k < 2 * m) {
+          const float4 fv = *reinterpret_cast<const float4*>(fs + k * n + x);
+          acc[r] = fmaf(fv.x, h0, fmaf(fv.y, h1, fmaf(fv.z, h2, fmaf(fv.w, h3, acc[r]))));
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int k = k0 + 8 * r;
+      if (k < 2 * m) Hx[(q * 2 * m + k) * CW + c] = acc[r];
+    }
+  }
+}
+
+// Inverse row transform for one (sample, y) row: s[x][c] = sum_k Bx[x][k] Z[k][c] over the
+// 2m kept (Re, Im) kx entries; each thread keeps its channel's Z column in registers.
+constexpr int MAXJ = 64;
+__global__ void __launch_bounds__(256) row_idft_kernel(const float* __restrict__ Z, const float* __restrict__ Bx,
+                                                       int n, int m, float* __restrict__ sout) {
+  extern __shared__ __align__(16) float bs[];   // [n][2m]
+  const long long q = blockIdx.x;
+  const int J = 2 * m;
+  for (int e = threadIdx.x; e < n * J / 4; e += 256) cp_async16(bs + 4 * e, Bx + 4 * e);
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+  const int c = threadIdx.x % CW, g = threadIdx.x / CW;
+  float z[MAXJ];
+#pragma unroll
+  for (int k = 0; k < MAXJ; ++k) z[k] = k < J ? Z[(q * J + k) * CW + c] : 0.f;
+  __syncthreads();
+  for (int x = g; x < n; x += 8) {
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < MAXJ; k += 4) {
+      if (k < J) {
+        const float4 bv = *reinterpret_cast<const float4*>(bs + x * J + k);
+        acc = fmaf(bv.x, z[k], fmaf(bv.y, z[k + 1], fmaf(bv.z, z[k + 2], fmaf(bv.w, z[k + 3], acc))));
+      }
+    }
+    sout[(q * n + x) * CW + c] = acc;
+  }
+}
+
+inline int row_idft_smem(int n, int m) { return n * 2 * m * 4; }
+
+inline int row_dft_smem(int n, int m) { return (n * CW + 2 * m * n) * 4; }
+
+// Column-local part of a spectral layer, for one (sample b, kx), in two kernels so that the
+// work spreads over many blocks (there are only m kx values per sample):
+//   column_fwd_mix_kernel, grid (kx, b, 2m/JB): H[j][c] = sum_y G[j][y] X[y][c] for JB kept ky
+//     rows (X = the row-DFT output column, G = exp(-2 pi i ky_j y / n)), written to global for
+//     the backward pass, then Y[j][o] = sum_i W[j][kx][i][o] H[j][i] (BF16 weights, FP32 sums);
+//   column_inv_kernel, grid (kx, b, n/YB): Z[y][c] = sum_j conj(G[j][y]) Y[j][c] for YB rows,
+//     stored as the Re | Im halves of each (b, y) row that the inverse row transform reads.
+constexpr int JB = 4, YB = 16;
+
+__global__ void __launch_bounds__(JB * CW) column_fwd_mix_kernel(
+    const float* __restrict__ Hx, const float* __restrict__ Gr, const float* __restrict__ Gi,
+    const __nv_bfloat16* __restrict__ Wr, const __nv_bfloat16* __restrict__ Wi, int n, int m,
+    float* __restrict__ Hr_out, float* __restrict__ Hi_out, float* __restrict__ Yr_out, float* __restrict__ Yi_out) {
+  extern __shared__ __align__(16) float sm[];
+  const int kx = blockIdx.x, b = blockIdx.y, j0 = blockIdx.z * JB, tid = threadIdx.x;
+  const int J = 2 * m;
+  const long long mC = (long long)m * CW, rowstride = 2 * mC;
+  float* xr = sm;
+  float* xi = xr + n * CW;
+  float* gr = xi + n * CW;     // [JB][n]
+  float* gi = gr + JB * n;
+  float* hr = gi + JB * n;     // [JB][C]
+  float* hi = hr + JB * CW;
+  const float* xb = Hx + (long long)b * n * rowstride + (long long)kx * CW;
+  for (int e = tid; e < n * (CW / 4); e += JB * CW) {
+    const int y = e / (CW / 4), c4 = (e % (CW / 4)) * 4;
+    cp_async16(xr + y * CW + c4, xb + (long long)y * rowstride + c4);
+    cp_async16(xi + y * CW + c4, xb + (long long)y * rowstride + mC + c4);
+  }
+  for (int e = tid; e < JB * n / 4; e += JB * CW) {
+    cp_async16(gr + 4 * e, Gr + (long long)j0 * n + 4 * e);
+    cp_async16(gi + 4 * e, Gi + (long long)j0 * n + 4 * e);
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+  const int c = tid % CW, jl = tid / CW, j = j0 + jl;
+  float ar = 0.f, ai = 0.f;
+#pragma unroll 8
+  for (int y = 0; y < n; ++y) {
+    const float a = gr[jl * n + y], bb = gi[jl * n + y];
+    const float u = xr[y * CW + c], v = xi[y * CW + c];
+    ar = fmaf(a, u, fmaf(-bb, v, ar));
+    ai = fmaf(a, v, fmaf(bb, u, ai));
+  }
+  hr[jl * CW + c] = ar;
+  hi[jl * CW + c] = ai;
+  const long long o = (((long long)b * J + j) * m + kx) * CW + c;
+  Hr_out[o] = ar;
+  Hi_out[o] = ai;
+  __syncwarp();
+  const __nv_bfloat16* wr = Wr + ((long long)j * m + kx) * CW * CW;
+  const __nv_bfloat16* wi = Wi + ((long long)j * m + kx) * CW * CW;
+  float yr = 0.f, yi = 0.f;
+#pragma unroll 16
+  for (int i = 0; i < CW; ++i) {
+    const float a = __bfloat162float(wr[i * CW + c]), bb = __bfloat162float(wi[i * CW + c]);
+    const float u = hr[jl * CW + i], v = hi[jl * CW + i];
+    yr = fmaf(a, u, fmaf(-bb, v, yr));
+    yi = fmaf(a, v, fmaf(bb, u, yi));
+  }
+  Yr_out[o] = yr;
+  Yi_out[o] = yi;
+}
+
+__global__ void __launch_bounds__(256) column_inv_kernel(const float* __restrict__ Yr, const float* __restrict__ Yi,
+                                                         const float* __restrict__ Gr, const float* __restrict__ Gi,
+                                                         int n, int m, float* __restrict__ Z) {
+  __shared__ float yr[64][CW], yi[64][CW];
+  const int kx = blockIdx.x, b = blockIdx.y, y0 = blockIdx.z * YB, tid = threadIdx.x;
+  const int J = 2 * m;
+  const long long mC = (long long)m * CW, rowstride = 2 * mC;
+  for (int e = tid; e < J * CW; e += 256) {
+    const int j = e / CW, c = e % CW;
+    const long long o = (((long long)b * J + j) * m + kx) * CW + c;
+    yr[j][c] = Yr[o];
+    yi[j][c] = Yi[o];
+  }
+  __syncthreads();
+  const int c = tid % CW;
+  float* zb = Z + (long long)b * n * rowstride + (long long)kx * CW;
+  for (int yl = tid / CW; yl < YB; yl += 256 / CW) {
+    const int y = y0 + yl;
+    float ar = 0.f, ai = 0.f;
+    for (int j = 0; j < J; ++j) {   // conj(G[j][y]) = Gr - i Gi
+      const float a = Gr[(long long)j * n + y], bb = -Gi[(long long)j * n + y];
+      ar = fmaf(a, yr[j][c], fmaf(-bb, yi[j][c], ar));
+      ai = fmaf(a, yi[j][c], fmaf(bb, yr[j][c], ai));
+    }
+    zb[(long long)y * rowstride + c] = ar;
+    zb[(long long)y * rowstride + mC + c] = ai;
+  }
+}
+
+inline int column_fwd_mix_smem(int n) { return (2 * n * CW + 2 * JB * n + 2 * JB * CW) * 4; }
+
+
 // Mode mixing, forward: Y[b][mode][o] = sum_i W[mode][i][o] H[b][mode][i] (complex, BF16 weights)
 __global__ void __launch_bounds__(CW) modemix_fwd_kernel(const float* __restrict__ Hr, const float* __restrict__ Hi,
                                                          const __nv_bfloat16* __restrict__ Wr,
@@ -478,6 +647,7 @@ struct ttsh_fno {
   double* lpart = nullptr;
   int wchunk, nwblk;
   float in_scale[4] = {1, 1, 1, 1}, out_scale = 1;
+  bool fused_columns = false;   // row_dft / column kernels fit in shared memory
   long long adam_t = 0;
   std::vector<void*> allocs;
 };
@@ -544,25 +714,43 @@ ttsh_status forward_impl(ttsh_fno* f, const float* x, int B, float* out, const f
   for (int l = 0; l < L; ++l) {
     const float* hl = f->h[l];
     // row DFT: Hx[q] (2m x C) = Fx (2m x n) . h[q] (n x C), q = (b, y)
-    FNO_CUDA(sgemm(false, false, 2 * m, C, n, B * n, 1.f, f->Fx, n, 0, hl, C, (long long)n * C, 0.f, f->Hx, C,
-                   2LL * m * C, s), "row DFT");
-    // column DFT per sample: H = G X (complex), X = Hx_b viewed as n x 2mC
+    if (f->fused_columns) {
+      row_dft_kernel<<<(unsigned)(B * n), 256, row_dft_smem(n, m), s>>>(hl, f->Fx, n, m, f->Hx);
+      FNO_CUDA(cudaGetLastError(), "row DFT");
+    } else {
+      FNO_CUDA(sgemm(false, false, 2 * m, C, n, B * n, 1.f, f->Fx, n, 0, hl, C, (long long)n * C, 0.f, f->Hx, C,
+                     2LL * m * C, s), "row DFT");
+    }
     const long long sX = (long long)n * 2 * mC, sH = 2LL * m * mC;
-    FNO_CUDA(sgemm(false, false, 2 * m, (int)mC, n, B, 1.f, f->Gr, n, 0, f->Hx, 2 * mC, sX, 0.f, f->Hr[l], mC, sH, s), "col DFT");
-    FNO_CUDA(sgemm(false, false, 2 * m, (int)mC, n, B, -1.f, f->Gi, n, 0, f->Hx + mC, 2 * mC, sX, 1.f, f->Hr[l], mC, sH, s), "col DFT");
-    FNO_CUDA(sgemm(false, false, 2 * m, (int)mC, n, B, 1.f, f->Gr, n, 0, f->Hx + mC, 2 * mC, sX, 0.f, f->Hi[l], mC, sH, s), "col DFT");
-    FNO_CUDA(sgemm(false, false, 2 * m, (int)mC, n, B, 1.f, f->Gi, n, 0, f->Hx, 2 * mC, sX, 1.f, f->Hi[l], mC, sH, s), "col DFT");
-    // mode mixing
-    modemix_fwd_kernel<<<nmodes, CW, 0, s>>>(f->Hr[l], f->Hi[l], f->wbf + f->boff_Wr[l], f->wbf + f->boff_Wi[l],
-                                             nmodes, B, f->Yr, f->Yi);
-    // inverse column: Z (n x mC complex, stored as Re | Im blocks of width mC) = G' Y
-    FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, 1.f, f->Gpr, 2 * m, 0, f->Yr, mC, sH, 0.f, f->Z, 2 * mC, sX, s), "inv col");
-    FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, -1.f, f->Gpi, 2 * m, 0, f->Yi, mC, sH, 1.f, f->Z, 2 * mC, sX, s), "inv col");
-    FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, 1.f, f->Gpr, 2 * m, 0, f->Yi, mC, sH, 0.f, f->Z + mC, 2 * mC, sX, s), "inv col");
-    FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, 1.f, f->Gpi, 2 * m, 0, f->Yr, mC, sH, 1.f, f->Z + mC, 2 * mC, sX, s), "inv col");
+    if (f->fused_columns) {
+      // column DFT + mode mixing (JB ky rows per block), then inverse column DFT (YB rows per block)
+      column_fwd_mix_kernel<<<dim3(m, B, 2 * m / JB), JB * CW, column_fwd_mix_smem(n), s>>>(
+          f->Hx, f->Gr, f->Gi, f->wbf + f->boff_Wr[l], f->wbf + f->boff_Wi[l], n, m, f->Hr[l], f->Hi[l], f->Yr, f->Yi);
+      column_inv_kernel<<<dim3(m, B, n / YB), 256, 0, s>>>(f->Yr, f->Yi, f->Gr, f->Gi, n, m, f->Z);
+      FNO_CUDA(cudaGetLastError(), "spectral column kernels");
+    } else {
+      // column DFT per sample: H = G X (complex), X = Hx_b viewed as n x 2mC
+      FNO_CUDA(sgemm(false, false, 2 * m, (int)mC, n, B, 1.f, f->Gr, n, 0, f->Hx, 2 * mC, sX, 0.f, f->Hr[l], mC, sH, s), "col DFT");
+      FNO_CUDA(sgemm(false, false, 2 * m, (int)mC, n, B, -1.f, f->Gi, n, 0, f->Hx + mC, 2 * mC, sX, 1.f, f->Hr[l], mC, sH, s), "col DFT");
+      FNO_CUDA(sgemm(false, false, 2 * m, (int)mC, n, B, 1.f, f->Gr, n, 0, f->Hx + mC, 2 * mC, sX, 0.f, f->Hi[l], mC, sH, s), "col DFT");
+      FNO_CUDA(sgemm(false, false, 2 * m, (int)mC, n, B, 1.f, f->Gi, n, 0, f->Hx, 2 * mC, sX, 1.f, f->Hi[l], mC, sH, s), "col DFT");
+      // mode mixing
+      modemix_fwd_kernel<<<nmodes, CW, 0, s>>>(f->Hr[l], f->Hi[l], f->wbf + f->boff_Wr[l], f->wbf + f->boff_Wi[l],
+                                               nmodes, B, f->Yr, f->Yi);
+      // inverse column: Z (n x mC complex, stored as Re | Im blocks of width mC) = G' Y
+      FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, 1.f, f->Gpr, 2 * m, 0, f->Yr, mC, sH, 0.f, f->Z, 2 * mC, sX, s), "inv col");
+      FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, -1.f, f->Gpi, 2 * m, 0, f->Yi, mC, sH, 1.f, f->Z, 2 * mC, sX, s), "inv col");
+      FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, 1.f, f->Gpr, 2 * m, 0, f->Yi, mC, sH, 0.f, f->Z + mC, 2 * mC, sX, s), "inv col");
+      FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, 1.f, f->Gpi, 2 * m, 0, f->Yr, mC, sH, 1.f, f->Z + mC, 2 * mC, sX, s), "inv col");
+    }
     // inverse row: s[q] (n x C) = Bx (n x 2m) . Z[q] (2m x C)
-    FNO_CUDA(sgemm(false, false, n, C, 2 * m, B * n, 1.f, f->Bx, 2 * m, 0, f->Z, C, 2LL * m * C, 0.f, f->s, C,
-                   (long long)n * C, s), "inv row");
+    if (f->fused_columns) {
+      row_idft_kernel<<<(unsigned)(B * n), 256, row_idft_smem(n, m), s>>>(f->Z, f->Bx, n, m, f->s);
+      FNO_CUDA(cudaGetLastError(), "inv row");
+    } else {
+      FNO_CUDA(sgemm(false, false, n, C, 2 * m, B * n, 1.f, f->Bx, 2 * m, 0, f->Z, C, 2LL * m * C, 0.f, f->s, C,
+                     (long long)n * C, s), "inv row");
+    }
     // z = h W + b + s on the tensor cores, then GELU
     PwArgs a;
     a.A = f->hb[l];
@@ -752,6 +940,18 @@ ttsh_status ttsh_fno_create(const ttsh_fno_config* cfg, uint64_t seed, void* str
   A(&f->wpart, (long long)f->nwblk * (C * C + C) * 4);
   A(&f->lpart, ((P + 255) / 256) * 8);
   if (e != cudaSuccess) return cleanup(fno_cuda(e, "FNO allocation"));
+  // the fused column kernel needs its plan in shared memory
+  if (column_fwd_mix_smem(n) <= 220 * 1024 && row_dft_smem(n, m) <= 220 * 1024 && 2 * m <= 64 &&
+      (2 * m) % JB == 0 && n % YB == 0) {
+    e = cudaFuncSetAttribute(column_fwd_mix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             column_fwd_mix_smem(n));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(row_dft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, row_dft_smem(n, m));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(row_idft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, row_idft_smem(n, m));
+    if (e != cudaSuccess) return cleanup(fno_cuda(e, "column kernel attribute"));
+    f->fused_columns = true;
+  }
   // DFT matrices on the kept modes
   {
     const double tp = 6.283185307179586476925286766559;
