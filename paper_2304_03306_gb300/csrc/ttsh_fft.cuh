@@ -169,11 +169,48 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
 }
 
+// Per-stage twiddle tables.  Stage (Ns, R) of a length-L transform multiplies input r of the
+// butterfly with sub-index k by W_TWN^{r k TWN/(Ns R)}; stored as [r - 1][k] (k fastest) those
+// reads are contiguous across a warp, where indexing one W_TWN table with stride r*k would
+// put many threads on the same bank.  Used when all stages' tables fit in 16 KB.
+__host__ __device__ constexpr int stage_radix(int L, int PE, int Ns) { return (L / Ns < PE) ? L / Ns : PE; }
+__host__ __device__ constexpr int stage_offset(int L, int PE, int NsTarget) {
+  int off = 0;
+  for (int Ns = 1; Ns < NsTarget; Ns *= stage_radix(L, PE, Ns))
+    if (Ns > 1) off += (stage_radix(L, PE, Ns) - 1) * Ns;
+  return off;
+}
+
+template <typename T, int L, int PE>
+struct StageTab {
+  static constexpr int ENTRIES = stage_offset(L, PE, L);
+  static constexpr bool USE = ENTRIES > 0 && ENTRIES * (int)sizeof(cplx<T>) <= 16384;
+  static constexpr int BYTES = USE ? (ENTRIES * (int)sizeof(cplx<T>) + 15) / 16 * 16 : 0;
+  // fill from the global W_TWN table (all threads; caller synchronises)
+  template <int TWN>
+  __device__ __forceinline__ static void fill(cplx<T>* sm, const cplx<T>* __restrict__ tw, int tid, int nt) {
+    if constexpr (USE) {
+      int off = 0;
+      for (int Ns = 1; Ns < L; Ns *= stage_radix(L, PE, Ns)) {
+        const int R = stage_radix(L, PE, Ns);
+        if (Ns > 1) {
+          const int stride = TWN / (Ns * R);
+          for (int i = tid; i < (R - 1) * Ns; i += nt) {
+            const int r = 1 + i / Ns, k = i % Ns;
+            sm[off + i] = tw[r * k * stride];
+          }
+          off += (R - 1) * Ns;
+        }
+      }
+    }
+  }
+};
+
 // One Stockham stage of radix R on a length-L transform at buf (padded), current
 // sub-transform length Ns.  j: this thread's index among the L/PE owners.
 template <typename T, int L, int PE, int R, int Ns, int DIR, int PS, int TWN>
 __device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
-                                               const TwTab<T, TWN>& tw) {
+                                               const TwTab<T, TWN>& tw, const cplx<T>* stab) {
   constexpr int TT = L / PE;
   constexpr int NB = PE / R;
   cplx<T> v[NB][R];
@@ -192,9 +229,19 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
       const int q = j + b * TT;
       const int k = q & (Ns - 1);
       if (Ns > 1) {
-        constexpr int stride = TWN / (Ns * R);
+        if constexpr (StageTab<T, L, PE>::USE) {
+          constexpr int off = stage_offset(L, PE, Ns);
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], twiddle<T, DIR>(tw, r * k * stride));
+          for (int r = 1; r < R; ++r) {
+            cplx<T> w = stab[off + (r - 1) * Ns + k];
+            if (DIR > 0) w.y = -w.y;
+            v[b][r] = cmul(v[b][r], w);
+          }
+        } else {
+          constexpr int stride = TWN / (Ns * R);
+#pragma unroll
+          for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], twiddle<T, DIR>(tw, r * k * stride));
+        }
       }
       dft_reg<T, R, DIR>(v[b]);
       const int base = (q - k) * R + k;
@@ -207,21 +254,22 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
 
 template <typename T, int L, int PE, int Ns, int DIR, int PS, int TWN>
 __device__ __forceinline__ void stockham_all(cplx<T>* buf, int j, bool active,
-                                             const TwTab<T, TWN>& tw) {
+                                             const TwTab<T, TWN>& tw, const cplx<T>* stab) {
   if constexpr (Ns < L) {
     constexpr int R = (L / Ns < PE) ? (L / Ns) : PE;
-    stockham_stage<T, L, PE, R, Ns, DIR, PS, TWN>(buf, j, active, tw);
-    stockham_all<T, L, PE, Ns * R, DIR, PS, TWN>(buf, j, active, tw);
+    stockham_stage<T, L, PE, R, Ns, DIR, PS, TWN>(buf, j, active, tw, stab);
+    stockham_all<T, L, PE, Ns * R, DIR, PS, TWN>(buf, j, active, tw, stab);
   }
 }
 
-// B transforms of length L laid out at sm + b * LP (padded), all threads of the block
-// participate (NT threads).  TWN: length of the twiddle table (a multiple of L).
+// B transforms of length L laid out at sm + b * STRIDE (padded; STRIDE = 0 means the padded
+// length), all threads of the block participate (NT threads).  TWN: length of the twiddle
+// table (a multiple of L); stab: this length's per-stage tables (ignored when unused).
 // Starts and ends with a block barrier.
-template <typename T, int L, int PE, int DIR, int NT, int TWN>
-__device__ __forceinline__ void fft_batch(cplx<T>* sm, int B, const TwTab<T, TWN>& tw) {
+template <typename T, int L, int PE, int DIR, int NT, int TWN, int STRIDE = 0>
+__device__ __forceinline__ void fft_batch(cplx<T>* sm, int B, const TwTab<T, TWN>& tw, const cplx<T>* stab) {
   constexpr int PS = ilog2(PE);
-  constexpr int LP = padded_len<L, PS>();
+  constexpr int LP = STRIDE > 0 ? STRIDE : padded_len<L, PS>();
   constexpr int TT = L / PE;
   static_assert(NT % TT == 0, "block size must be a multiple of the threads per transform");
   constexpr int PER = NT / TT;
@@ -231,7 +279,7 @@ __device__ __forceinline__ void fft_batch(cplx<T>* sm, int B, const TwTab<T, TWN
   for (int c0 = 0; c0 < B; c0 += PER) {
     const int b = c0 + slot;
     const bool active = b < B;
-    stockham_all<T, L, PE, 1, DIR, PS, TWN>(sm + (active ? b : 0) * LP, j, active, tw);
+    stockham_all<T, L, PE, 1, DIR, PS, TWN>(sm + (active ? b : 0) * LP, j, active, tw, stab);
   }
 }
 

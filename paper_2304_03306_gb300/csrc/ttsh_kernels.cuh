@@ -74,6 +74,12 @@ __host__ __device__ constexpr int default_row_pe() { return sizeof(T) == 4 ? 16 
 template <typename T, int N>
 __host__ __device__ constexpr int default_col_pe() { return sizeof(T) == 4 ? (N <= 1024 ? 8 : 16) : 8; }
 
+// Stride between the row buffers of one block: R-strided accesses (prep writes, post reads)
+// land on distinct banks when consecutive rows are 32/R banks apart.
+__host__ __device__ constexpr int row_stride(int LP, int R, int words) {
+  return R == 1 ? LP : LP + ((((32 / R) / words) % (32 / words) - LP % (32 / words)) % (32 / words) + (32 / words)) % (32 / words);
+}
+
 // Row-pass geometry and shared-memory plan.
 template <typename T, int N, int KIND, int R, int PEV>
 struct RowGeo {
@@ -87,8 +93,10 @@ struct RowGeo {
   static constexpr int F = cmax(FI, FF);
   static constexpr int NPL = FI == 0 ? 0 : (KIND == ROW_INV_MASK ? 1 : 4);   // G planes read
   static constexpr int CB = (int)sizeof(cplx<T>);
-  static constexpr int TW_BYTES = align16(TwTab<T, N>::ENTRIES * CB);
-  static constexpr int BUF_BYTES = F * R * LP * CB;
+  static constexpr int LPR = row_stride(LP, R, CB / 4);
+  static constexpr int TW_BYTES = align16(TwTab<T, N>::ENTRIES * CB) + StageTab<T, L, PE>::BYTES;
+  static constexpr int OFF_STAB = align16(TwTab<T, N>::ENTRIES * CB);
+  static constexpr int BUF_BYTES = F * R * LPR * CB;
   static constexpr int GIN_BYTES = NPL * H * R * CB;
   static constexpr int KS_BYTES = KIND == ROW_STEP ? R * N * (int)sizeof(T) : 0;
   static constexpr int RED_BYTES = KIND == ROW_INV_DIAG ? kDiagQ * 1024 * 8 : 0;
@@ -117,7 +125,8 @@ struct ColGeo {
   static constexpr int NF = MODE == COL_STEP ? 3 : MODE == COL_PROJECT ? 2 : (MODE == COL_MASK || MODE == COL_ADDW) ? 1 : 0;
   static constexpr int NI = MODE == COL_MASK ? 1 : 4;
   static constexpr int CB = (int)sizeof(cplx<T>);
-  static constexpr int TW_BYTES = align16(TwTab<T, N>::ENTRIES * CB);
+  static constexpr int TW_BYTES = align16(TwTab<T, N>::ENTRIES * CB) + StageTab<T, N, PE>::BYTES;
+  static constexpr int OFF_STAB = align16(TwTab<T, N>::ENTRIES * CB);
   static constexpr int ACC_BYTES = align16(NK * CB);
   static constexpr int WS_BYTES = (MODE == COL_STEP || MODE == COL_ADDW) ? align16(NK * CB) : 0;
   static constexpr int FIXED = TW_BYTES + ACC_BYTES + WS_BYTES + 64;
@@ -141,7 +150,7 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
   using Geo = RowGeo<T, N, KIND, R, PEV>;
   static_assert(Geo::VALID, "row pass tile does not fit");
   constexpr int L = Geo::L, M = Geo::M, H = Geo::H;
-  constexpr int NT = Geo::NT, PE = Geo::PE, PS = Geo::PS, LP = Geo::LP;
+  constexpr int NT = Geo::NT, PE = Geo::PE, PS = Geo::PS, LP = Geo::LPR;
   constexpr int FI = Geo::FI, FF = Geo::FF;
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_BUF);
   cplx<T>* gin = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_GIN);
@@ -151,9 +160,11 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
 
   // ---- stage: twiddles, the G tile (R consecutive y of every stored column), the K rows ----
   const TwTab<T, N> tw = TwTab<T, N>::fill(reinterpret_cast<cplx<T>*>(smem_raw), A.tw, tid, NT);
+  cplx<T>* stab = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_STAB);
+  StageTab<T, L, PE>::template fill<N>(stab, A.tw, tid, NT);
   if constexpr (Geo::STAGE_G) {
     constexpr int CPS = Geo::SEG / Geo::CHUNK;   // chunks per segment
-    constexpr int PLANE0 = (KIND == ROW_INV_MASK) ? 0 : 0;
+    constexpr int PLANE0 = 0;
     for (int i = tid; i < Geo::NPL * H * CPS; i += NT) {
       const int c = i % CPS;
       const int t = i / CPS;                     // t = pl * H + kx
@@ -208,7 +219,7 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
       const cplx<T> d = X - conjg(Xm);
       sm[(f * R + r) * LP + padi<PS>(k)] = s + mul_i(cmul(w, d));
     }
-    fft_batch<T, L, PE, +1, NT, N>(sm, FI * R, tw);
+    fft_batch<T, L, PE, +1, NT, N, LP>(sm, FI * R, tw, stab);
   }
 
   // ---- real-space work ----
@@ -282,7 +293,7 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
 
   // ---- forward row transforms (R2C), keep mx <= N/4 ----
   if constexpr (FF > 0) {
-    fft_batch<T, L, PE, -1, NT, N>(sm, FF * R, tw);
+    fft_batch<T, L, PE, -1, NT, N, LP>(sm, FF * R, tw, stab);
     for (int e = tid; e < FF * R * H; e += NT) {
       const int r = e % R;
       const int t = e / R;
@@ -319,6 +330,8 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
   constexpr int CB = Geo::CB;
 
   const TwTab<T, N> tw = TwTab<T, N>::fill(reinterpret_cast<cplx<T>*>(smem_raw), A.tw, tid, NT);
+  cplx<T>* stab = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_STAB);
+  StageTab<T, N, PE>::template fill<N>(stab, A.tw, tid, NT);
   auto ky_of = [](int j) { return j <= M ? j : j - NK; };
   // async copy of nb contiguous columns of Rr (fields f0..f0+nb-1) into the padded buffers
   auto stage_columns = [&](int f0, int nb) {
@@ -338,7 +351,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
       const int nb = cmin(FB, NF - f0);
       stage_columns(f0, nb);
       cp_async_wait_all();
-      fft_batch<T, N, PE, -1, NT, N>(buf, nb, tw);
+      fft_batch<T, N, PE, -1, NT, N>(buf, nb, tw, stab);
       for (int j = tid; j < NK; j += NT) {
         const int ky = ky_of(j);
         const int idx = ky & (N - 1);
@@ -459,7 +472,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
       }
       buf[b * LP + padi<PS>(idx)] = v;
     }
-    fft_batch<T, N, PE, +1, NT, N>(buf, nb, tw);
+    fft_batch<T, N, PE, +1, NT, N>(buf, nb, tw, stab);
     for (int e = tid; e < nb * N; e += NT) {
       const int b = e / N, y = e % N;
       A.G[((size_t)(f0 + b) * H + kx) * N + y] = buf[b * LP + padi<PS>(y)];
