@@ -208,6 +208,26 @@ ttsh_status ttsh_batch_synchronize(ttsh_batch* b);
 int32_t ttsh_batch_groups(const ttsh_batch* b);   /* number of launch groups, -1 if NULL */
 void ttsh_batch_destroy(ttsh_batch* b);           /* NULL is a no-op; domains are untouched */
 
+/* Temporal power spectral density of the vorticity, Eq. (PSD) of Sec. III.B:
+ *   S(W) = N^-2 sum_x |sum_t omega(x, t) exp(-i W t)|^2,
+ * summed over the snapshots passed to ttsh_psd_accumulate.  ttsh_psd_begin sets the nfreq
+ * angular frequencies W (host array, nfreq in [1, 4096]) and clears the accumulators (it
+ * allocates 2 * nfreq * H * NK complex doubles plus small buffers, freed with the domain);
+ * ttsh_psd_accumulate(t) adds the current state at time t (asynchronous); ttsh_psd_result
+ * writes the nfreq values of S to the host (synchronises).  Computed on the spectral state
+ * through Parseval in double precision, so it equals the real-space definition to rounding. */
+ttsh_status ttsh_psd_begin(ttsh_domain* d, const double* omegas, int32_t nfreq);
+ttsh_status ttsh_psd_accumulate(ttsh_domain* d, double t);
+ttsh_status ttsh_psd_result(ttsh_domain* d, double* S);
+
+/* Dumbbell order parameter of Sec. IV.B:
+ *   Psi_2 = |omega(x*_L) + omega(x*_R)| / (|omega(x*_L)| + |omega(x*_R)|),
+ * x*_{L,R} = argmax |omega| over the grid points within `radius` (= D/2, closed disc) of the
+ * cavity centres (centres = {xL, yL, xR, yR}); ties go to the first point in row-major
+ * order.  out[0] = Psi_2, out[1] = omega(x*_L), out[2] = omega(x*_R).  TTSH_E_INVALID if a
+ * disc holds no grid point.  Double precision; synchronises. */
+ttsh_status ttsh_dumbbell_order(ttsh_domain* d, const double* centres, double radius, double* out);
+
 /* Spectral restriction of a fine domain's state onto a coarse domain covering the same box
  * (n_fine * dx_fine == n_coarse * dx_coarse, n_coarse <= n_fine, same precision): the coarse
  * unitary coefficients are the fine ones times n_coarse/n_fine on the coarse 1/2-rule disc,

@@ -278,3 +278,37 @@ def diagnostics(s: State, p: Params, center=(0.0, 0.0), nbins: int | None = None
     if nbins is not None:
         d["spectrum"] = shell_spectrum(s, p, nbins)
     return d
+
+
+# ----------------------------------------------------------------------------------------
+# Dynamics diagnostics of Sec. III.B and Sec. IV.B
+# ----------------------------------------------------------------------------------------
+
+def temporal_psd(fields, times, omegas) -> np.ndarray:
+    """S(Omega) = N^-2 sum_x |sum_t omega(x, t) exp(-i Omega t)|^2 (Eq. PSD, Sec. III.B),
+    for real vorticity snapshots `fields` taken at `times`."""
+    n = fields[0].shape[0]
+    out = []
+    for Om in omegas:
+        A = np.zeros((n, n), dtype=complex)
+        for w, t in zip(fields, times):
+            A += w * np.exp(-1j * Om * t)
+        out.append(np.sum(np.abs(A) ** 2) / (n * n))
+    return np.array(out)
+
+
+def dumbbell_order_parameter(omega, p: Params, centres, radius):
+    """Psi_2 = |omega(x*_L) + omega(x*_R)| / (|omega(x*_L)| + |omega(x*_R)|) (Sec. IV.B), where
+    x*_{L,R} = argmax |omega| over the grid points within `radius` (= D/2) of each cavity
+    centre.  Readings: the disc is closed (distance <= radius); ties go to the first point in
+    row-major [y][x] order.  Returns (Psi_2, omega(x*_L), omega(x*_R))."""
+    n = p.n
+    c = (np.arange(n, dtype=np.float64) - n // 2) * p.dx
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    peaks = []
+    for cx, cy in centres:
+        region = (X - cx) ** 2 + (Y - cy) ** 2 <= radius * radius
+        flat = np.where(region.reshape(-1), np.abs(omega).reshape(-1), -1.0)
+        peaks.append(float(omega.reshape(-1)[int(np.argmax(flat))]))
+    a, b = peaks
+    return abs(a + b) / (abs(a) + abs(b)), a, b

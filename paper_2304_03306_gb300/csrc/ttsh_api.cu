@@ -10,6 +10,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <unordered_set>
@@ -64,7 +65,8 @@ Layout layout_for(int n, size_t elt) {
   L.Rr = take(3 * H * n * 2 * elt);
   L.tw = take((size_t)n * 2 * elt);
   L.real = take(3 * NN * sizeof(double));
-  L.part = take((size_t)n * ttsh::kDiagQ * sizeof(double));
+  // row-block diagnostic partials; also holds the 2 x 120 peak partials of ttsh_dumbbell_order
+  L.part = take(std::max((size_t)n * ttsh::kDiagQ * sizeof(double), (size_t)8192));
   L.colhist = take(H * (M + 1) * sizeof(double));
   L.bad = take(64);
   L.out = take((8 + M + 1) * sizeof(double));
@@ -122,6 +124,11 @@ struct ttsh_domain {
   cudaGraphExec_t graph;
   int graph_len;
   int rv, cv;   // selected tile shapes of the row and column step kernels
+  // temporal power spectral density accumulators (ttsh_psd_*)
+  int psd_nfreq = 0;
+  double* psd_omega = nullptr;   // nfreq angular frequencies
+  double2* psd_acc = nullptr;    // [2][nfreq][H*NK]: sums with exp(-i W t) and exp(+i W t)
+  double* psd_S = nullptr;       // nfreq results
 };
 
 namespace {
@@ -328,6 +335,109 @@ __global__ void restrict_kernel(const cplx<T>* __restrict__ wf, const T* __restr
     vc[1] = vf[1] * s;
   }
 }
+
+// ---- dynamics diagnostics: temporal PSD (Eq. PSD) and the dumbbell order parameter ----
+// PSD: S(W) = N^-2 sum_x |sum_t omega(x,t) e^{-iWt}|^2 = N^-2 sum_k |sum_t omega^(k,t) e^{-iWt}|^2
+// (Parseval, unitary DFT).  Only mx >= 0 is stored; the mode -k of the accumulated sum is
+// conj(sum_t omega^(k,t) e^{+iWt}), so for mx > 0 both sums are kept.
+template <typename T>
+__global__ void psd_accumulate_kernel(const cplx<T>* __restrict__ what, int nmodes, const double* __restrict__ om,
+                                      double t, double2* __restrict__ acc, int nfreq) {
+  __shared__ double cs[2];
+  const int j = blockIdx.y;
+  if (threadIdx.x == 0) sincos(om[j] * t, &cs[1], &cs[0]);
+  __syncthreads();
+  const double c = cs[0], sn = cs[1];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nmodes; i += gridDim.x * blockDim.x) {
+    const double wr = (double)what[i].x, wi = (double)what[i].y;
+    double2& a = acc[(size_t)j * nmodes + i];
+    double2& b = acc[((size_t)nfreq + j) * nmodes + i];
+    a.x += wr * c + wi * sn;   // (wr + i wi)(c - i s)
+    a.y += wi * c - wr * sn;
+    b.x += wr * c - wi * sn;   // (wr + i wi)(c + i s)
+    b.y += wi * c + wr * sn;
+  }
+}
+
+__global__ void psd_result_kernel(const double2* __restrict__ acc, int NK, int nmodes, int nfreq, double scale,
+                                  double* __restrict__ S) {
+  __shared__ double red[256];
+  const int j = blockIdx.x, t = threadIdx.x;
+  double sum = 0.0;
+  for (int i = t; i < nmodes; i += 256) {
+    const double2 a = acc[(size_t)j * nmodes + i];
+    sum += a.x * a.x + a.y * a.y;
+    if (i >= NK) {   // mx > 0: the mirrored mode
+      const double2 b = acc[((size_t)nfreq + j) * nmodes + i];
+      sum += b.x * b.x + b.y * b.y;
+    }
+  }
+  red[t] = sum;
+  __syncthreads();
+  for (int s2 = 128; s2 >= 1; s2 >>= 1) {
+    if (t < s2) red[t] += red[t + s2];
+    __syncthreads();
+  }
+  if (t == 0) S[j] = red[0] * scale;
+}
+
+// Psi_2: per-block argmax of |omega| inside the closed discs around the two cavity centres
+// (ties to the smaller row-major index), then a single-block final reduction.
+struct Peak {
+  double absval, val;
+  long long idx;
+};
+__device__ __forceinline__ bool better(const Peak& a, const Peak& b) {
+  return a.absval > b.absval || (a.absval == b.absval && a.idx < b.idx);
+}
+
+__global__ void dumbbell_partial_kernel(const double* __restrict__ w, int n, double dx, double c0x, double c0y,
+                                        double c1x, double c1y, double r2, Peak* __restrict__ part) {
+  __shared__ Peak red[2][256];
+  Peak best[2] = {{-1.0, 0.0, -1}, {-1.0, 0.0, -1}};
+  const long long total = (long long)n * n;
+  for (long long p = blockIdx.x * 256LL + threadIdx.x; p < total; p += 256LL * gridDim.x) {
+    const int ix = (int)(p % n), iy = (int)(p / n);
+    const double x = (double)(ix - n / 2) * dx, y = (double)(iy - n / 2) * dx;
+    const double v = w[p];
+    const double cx[2] = {c0x, c1x}, cy[2] = {c0y, c1y};
+    for (int c = 0; c < 2; ++c) {
+      const double ddx = __dsub_rn(x, cx[c]), ddy = __dsub_rn(y, cy[c]);
+      const double d2 = __dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy));
+      if (d2 <= r2) {
+        const Peak cand{fabs(v), v, p};
+        if (better(cand, best[c])) best[c] = cand;
+      }
+    }
+  }
+  red[0][threadIdx.x] = best[0];
+  red[1][threadIdx.x] = best[1];
+  __syncthreads();
+  for (int s2 = 128; s2 >= 1; s2 >>= 1) {
+    if (threadIdx.x < s2)
+      for (int c = 0; c < 2; ++c)
+        if (better(red[c][threadIdx.x + s2], red[c][threadIdx.x])) red[c][threadIdx.x] = red[c][threadIdx.x + s2];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = red[0][0];
+    part[2 * blockIdx.x + 1] = red[1][0];
+  }
+}
+
+__global__ void dumbbell_final_kernel(const Peak* __restrict__ part, int nblocks, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  Peak b[2] = {{-1.0, 0.0, -1}, {-1.0, 0.0, -1}};
+  for (int i = 0; i < nblocks; ++i)
+    for (int c = 0; c < 2; ++c)
+      if (better(part[2 * i + c], b[c])) b[c] = part[2 * i + c];
+  const double a = b[0].val, bb = b[1].val;
+  const double den = fabs(a) + fabs(bb);
+  out[0] = den > 0 ? fabs(a + bb) / den : 0.0;
+  out[1] = a;
+  out[2] = bb;
+  out[3] = (b[0].idx < 0 || b[1].idx < 0) ? 1.0 : 0.0;   // an empty region
+}
 }  // namespace ttsh
 
 // ---------------------------------------------------------------------------------------
@@ -529,6 +639,9 @@ ttsh_status ttsh_create_domain(const uint8_t* mask, const ttsh_params* p, void* 
 
 void ttsh_destroy_domain(ttsh_domain* d) {
   if (!d) return;
+  if (d->psd_omega) cudaFree(d->psd_omega);
+  if (d->psd_acc) cudaFree(d->psd_acc);
+  if (d->psd_S) cudaFree(d->psd_S);
   if (d->graph) cudaGraphExecDestroy(d->graph);
   if (d->capture) cudaStreamDestroy(d->capture);
   if (d->owns_ws && d->ws) cudaFree(d->ws);
@@ -885,6 +998,81 @@ ttsh_status ttsh_restrict(const ttsh_domain* fine, ttsh_domain* coarse) {
   if (st != TTSH_OK) return st;
   coarse->steps = 0;
   TTSH_CUDA(cudaStreamSynchronize(coarse->stream), "restrict");
+  return TTSH_OK;
+}
+
+
+ttsh_status ttsh_psd_begin(ttsh_domain* d, const double* omegas, int32_t nfreq) {
+  if (!d || !omegas) return fail(TTSH_E_INVALID, "NULL argument");
+  if (nfreq < 1 || nfreq > 4096) return fail(TTSH_E_INVALID, "nfreq must be in [1, 4096]");
+  if (d->psd_omega) cudaFree(d->psd_omega);
+  if (d->psd_acc) cudaFree(d->psd_acc);
+  if (d->psd_S) cudaFree(d->psd_S);
+  if (d->psd_S) cudaFree(d->psd_S);
+  d->psd_omega = nullptr;
+  d->psd_acc = nullptr;
+  d->psd_S = nullptr;
+  d->psd_nfreq = 0;
+  const size_t nm = (size_t)d->H * d->NK;
+  TTSH_CUDA(cudaMalloc(&d->psd_omega, nfreq * sizeof(double)), "PSD allocation");
+  TTSH_CUDA(cudaMalloc(&d->psd_S, nfreq * sizeof(double)), "PSD allocation");
+  TTSH_CUDA(cudaMalloc(&d->psd_acc, 2 * (size_t)nfreq * nm * sizeof(double2)), "PSD allocation");
+  TTSH_CUDA(cudaMemcpyAsync(d->psd_omega, omegas, nfreq * sizeof(double), cudaMemcpyHostToDevice, d->stream), "PSD upload");
+  TTSH_CUDA(cudaMemsetAsync(d->psd_acc, 0, 2 * (size_t)nfreq * nm * sizeof(double2), d->stream), "PSD clear");
+  d->psd_nfreq = nfreq;
+  return sync(d, "psd_begin");
+}
+
+ttsh_status ttsh_psd_accumulate(ttsh_domain* d, double t) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  if (!d->psd_nfreq) return fail(TTSH_E_INVALID, "ttsh_psd_begin was not called");
+  const int nm = d->H * d->NK;
+  dim3 grid((nm + 255) / 256, d->psd_nfreq);
+  if (d->elt == sizeof(float))
+    ttsh::psd_accumulate_kernel<float><<<grid, 256, 0, d->stream>>>((const ttsh::cplx<float>*)d->dev.what, nm,
+                                                                    d->psd_omega, t, d->psd_acc, d->psd_nfreq);
+  else
+    ttsh::psd_accumulate_kernel<double><<<grid, 256, 0, d->stream>>>((const ttsh::cplx<double>*)d->dev.what, nm,
+                                                                     d->psd_omega, t, d->psd_acc, d->psd_nfreq);
+  TTSH_CUDA(cudaGetLastError(), "PSD accumulate");
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_psd_result(ttsh_domain* d, double* S) {
+  if (!d || !S) return fail(TTSH_E_INVALID, "NULL argument");
+  if (!d->psd_nfreq) return fail(TTSH_E_INVALID, "ttsh_psd_begin was not called");
+  const double scale = 1.0 / ((double)d->n * (double)d->n);
+  ttsh::psd_result_kernel<<<d->psd_nfreq, 256, 0, d->stream>>>(d->psd_acc, d->NK, d->H * d->NK, d->psd_nfreq,
+                                                               scale, d->psd_S);
+  TTSH_CUDA(cudaGetLastError(), "PSD result");
+  std::vector<double> h(d->psd_nfreq);
+  TTSH_CUDA(cudaMemcpyAsync(h.data(), d->psd_S, d->psd_nfreq * sizeof(double), cudaMemcpyDeviceToHost, d->stream),
+            "PSD result");
+  ttsh_status st = sync(d, "psd_result");
+  if (st != TTSH_OK) return st;
+  for (int j = 0; j < d->psd_nfreq; ++j) S[j] = h[j];
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_dumbbell_order(ttsh_domain* d, const double* centres, double radius, double* out) {
+  if (!d || !centres || !out) return fail(TTSH_E_INVALID, "NULL argument");
+  if (!(radius > 0)) return fail(TTSH_E_INVALID, "radius must be positive");
+  ttsh_status st = run_row(d, ttsh::K_ROW_INV_FIELDS, d->stream);
+  if (st != TTSH_OK) return st;
+  const int nblk = 120;
+  static_assert(sizeof(ttsh::Peak) * 2 * 120 <= 8192, "peak partials fit the partials region");
+  ttsh::Peak* part = reinterpret_cast<ttsh::Peak*>(d->dev.part);
+  ttsh::dumbbell_partial_kernel<<<nblk, 256, 0, d->stream>>>(d->dev.real, d->n, d->p.dx, centres[0], centres[1],
+                                                             centres[2], centres[3], radius * radius, part);
+  ttsh::dumbbell_final_kernel<<<1, 32, 0, d->stream>>>(part, nblk, d->dev.out);
+  TTSH_CUDA(cudaGetLastError(), "dumbbell order");
+  double h[4];
+  TTSH_CUDA(cudaMemcpyAsync(h, d->dev.out, sizeof(h), cudaMemcpyDeviceToHost, d->stream), "dumbbell order");
+  if ((st = sync(d, "dumbbell_order")) != TTSH_OK) return st;
+  if (h[3] != 0.0) return fail(TTSH_E_INVALID, "a cavity disc contains no grid point");
+  out[0] = h[0];
+  out[1] = h[1];
+  out[2] = h[2];
   return TTSH_OK;
 }
 

@@ -172,7 +172,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // Per-stage twiddle tables.  Stage (Ns, R) of a length-L transform multiplies input r of the
 // butterfly with sub-index k by W_TWN^{r k TWN/(Ns R)}; stored as [r - 1][k] (k fastest) those
 // reads are contiguous across a warp, where indexing one W_TWN table with stride r*k would
-// put many threads on the same bank.  Used when all stages' tables fit in 16 KB.
+// put many threads on the same bank.  Used when all stages' tables fit in 32 KB.
 __host__ __device__ constexpr int stage_radix(int L, int PE, int Ns) { return (L / Ns < PE) ? L / Ns : PE; }
 __host__ __device__ constexpr int stage_offset(int L, int PE, int NsTarget) {
   int off = 0;
@@ -184,7 +184,7 @@ __host__ __device__ constexpr int stage_offset(int L, int PE, int NsTarget) {
 template <typename T, int L, int PE>
 struct StageTab {
   static constexpr int ENTRIES = stage_offset(L, PE, L);
-  static constexpr bool USE = ENTRIES > 0 && ENTRIES * (int)sizeof(cplx<T>) <= 16384;
+  static constexpr bool USE = ENTRIES > 0 && ENTRIES * (int)sizeof(cplx<T>) <= 32768;
   static constexpr int BYTES = USE ? (ENTRIES * (int)sizeof(cplx<T>) + 15) / 16 * 16 : 0;
   // fill from the global W_TWN table (all threads; caller synchronises)
   template <int TWN>

@@ -86,6 +86,10 @@ def load_library(path: str = LIB_PATH):
         "ttsh_batch_groups": (ctypes.c_int32, [_P]),
         "ttsh_batch_destroy": (None, [_P]),
         "ttsh_restrict": (ctypes.c_int, [_P, _P]),
+        "ttsh_psd_begin": (ctypes.c_int, [_P, _D, ctypes.c_int32]),
+        "ttsh_psd_accumulate": (ctypes.c_int, [_P, ctypes.c_double]),
+        "ttsh_psd_result": (ctypes.c_int, [_P, _D]),
+        "ttsh_dumbbell_order": (ctypes.c_int, [_P, _D, ctypes.c_double, _D]),
         "ttsh_fno_create": (ctypes.c_int, [ctypes.POINTER(ttsh_fno_config), ctypes.c_uint64, _P, ctypes.POINTER(_P)]),
         "ttsh_fno_destroy": (None, [_P]),
         "ttsh_fno_num_params": (ctypes.c_int64, [_P]),
@@ -299,6 +303,28 @@ class Batch:
             pass
 
 
+def ttsh_psd_begin(h, omegas):
+    om = np.ascontiguousarray(omegas, dtype=np.float64)
+    _check(load_library().ttsh_psd_begin(h, _dptr(om), int(om.size)))
+
+
+def ttsh_psd_accumulate(h, t: float):
+    _check(load_library().ttsh_psd_accumulate(h, float(t)))
+
+
+def ttsh_psd_result(h, nfreq: int):
+    S = np.empty(nfreq)
+    _check(load_library().ttsh_psd_result(h, _dptr(S)))
+    return S
+
+
+def ttsh_dumbbell_order(h, centres, radius: float):
+    c = np.ascontiguousarray(centres, dtype=np.float64).reshape(4)
+    out = np.empty(3)
+    _check(load_library().ttsh_dumbbell_order(h, _dptr(c), float(radius), _dptr(out)))
+    return float(out[0]), float(out[1]), float(out[2])
+
+
 def ttsh_restrict(fine, coarse):
     _check(load_library().ttsh_restrict(fine, coarse))
 
@@ -452,3 +478,17 @@ class Domain:
     @property
     def steps(self) -> int:
         return ttsh_step_count(self.h)
+
+    def psd_begin(self, omegas):
+        self._psd_n = len(omegas)
+        ttsh_psd_begin(self.h, omegas)
+
+    def psd_accumulate(self, t: float):
+        ttsh_psd_accumulate(self.h, t)
+
+    def psd_result(self):
+        return ttsh_psd_result(self.h, self._psd_n)
+
+    def dumbbell_order(self, centres, radius: float):
+        """(Psi_2, omega at the left peak, omega at the right peak)."""
+        return ttsh_dumbbell_order(self.h, centres, radius)

@@ -392,3 +392,58 @@ def test_batch_rejects_bad_input(T):
     with pytest.raises(T.TTSHError) as e:
         T.Batch([d, big])
     assert e.value.status == T.TTSH_E_UNSUPPORTED
+
+
+# ----------------------------------------- arbitrary boundary shapes (binary image input)
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_arbitrary_shape_with_obstacle_matches_oracle(T, prec):
+    n, dx = 128, 0.16
+    mask = ti.blob_mask(n, dx, seed=17)
+    assert 0.2 < mask.mean() < 0.95                       # a real interior and a real wall
+    dom, p, K, s = setup(T, n, dx, None, prec, 23, amp=0.3, mask=mask)
+    assert np.abs(dom.mask() - K).max() <= (1e-13 if prec == 64 else 2e-6)
+    dom.step(60)
+    s = O.run(s, K, p, 60)
+    check_fields(dom, s, TOL[prec])
+
+
+# ------------------------------------------- temporal PSD and dumbbell order parameter
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_temporal_psd_matches_definition(T, prec):
+    n, dx = 64, 0.25
+    dom, p, K, s = setup(T, n, dx, 5.6, prec, 31, amp=0.3)
+    omegas = np.linspace(0.0, 3.0, 7)
+    dom.psd_begin(omegas)
+    fields, times = [], []
+    for k in range(6):
+        dom.step(15)
+        t = 15 * (k + 1) * p.dt
+        dom.psd_accumulate(t)
+        fields.append(dom.fields()[2])
+        times.append(t)
+    S = dom.psd_result()
+    ref = O.temporal_psd(fields, times, omegas)          # the definition on the GPU's own fields
+    np.testing.assert_allclose(S, ref, rtol=1e-11 if prec == 64 else 2e-6)
+    traj = []
+    for _ in range(6):
+        s = O.run(s, K, p, 15)
+        traj.append(O.vorticity(s))
+    np.testing.assert_allclose(S, O.temporal_psd(traj, times, omegas), rtol=TOL[prec] * 10)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_dumbbell_order_parameter_matches_definition(T, prec):
+    n, dx, R, D = 128, 0.08, 3.0, 4.2
+    mask = ti.dumbbell_mask(n, dx, R, D)
+    dom, p, K, s = setup(T, n, dx, None, prec, 37, amp=0.3, mask=mask)
+    dom.step(40)
+    centres = [(-D / 2, 0.0), (D / 2, 0.0)]
+    psi2, a, b = dom.dumbbell_order(np.array(centres).reshape(-1), D / 2)
+    w = dom.fields()[2]
+    ref = O.dumbbell_order_parameter(w, p, centres, D / 2)
+    assert (a, b) == (ref[1], ref[2])                     # the same peaks, exactly
+    assert psi2 == pytest.approx(ref[0], rel=1e-14, abs=1e-15)
+    with pytest.raises(T.TTSHError):
+        dom.dumbbell_order(np.array([0.01, 0.01, 0.02, 0.0]), 1e-4)   # a disc with no grid point

@@ -399,3 +399,51 @@ def test_noise_only_inside_mask():
     assert np.all(vx[mask == 1] == 0) and np.all(vy[mask == 1] == 0)
     assert np.abs(vx).max() <= 0.01 and np.abs(vx[mask == 0]).min() >= 0
     assert abs(vx[mask == 0].mean()) < 0.002
+
+
+# ---------------------------------------------------------- PSD and Psi_2 (Sec. III.B, IV.B)
+
+def test_temporal_psd_of_a_single_frequency():
+    """omega = f(x) cos(W0 t + phi) sampled at t_j = j dt, j < T, with W0 T dt a multiple of pi:
+    sum_t omega e^{-i W0 t} = (T/2) e^{i phi} f, so S(W0) = (T/2)^2 N^-2 sum f^2, while a
+    frequency on the same grid away from +-W0 gives 0."""
+    n, T, dt = 16, 40, 0.25
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal((n, n))
+    W0 = 2 * np.pi * 3 / (T * dt)
+    times = np.arange(T) * dt
+    fields = [f * np.cos(W0 * t + 0.7) for t in times]
+    S = O.temporal_psd(fields, times, [W0, 2 * np.pi * 5 / (T * dt)])
+    assert S[0] == pytest.approx((T / 2) ** 2 * np.sum(f * f) / (n * n), rel=1e-12)
+    assert abs(S[1]) <= 1e-20 * S[0] + 1e-22
+
+
+def _two_peaks(p, centres, amps, width=0.6):
+    X, Y = coords(p)
+    w = np.zeros((p.n, p.n))
+    for (cx, cy), a in zip(centres, amps):
+        w += a * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / width ** 2)
+    return w
+
+
+@pytest.mark.parametrize("amps,expect", [((1.0, 1.0), 1.0), ((1.0, -1.0), 0.0), ((2.0, -0.5), 0.6),
+                                         ((-0.3, -0.9), 1.0)])
+def test_dumbbell_order_parameter_closed_forms(amps, expect):
+    p = O.Params(n=64, dx=0.25)
+    centres = [(-2.0, 0.0), (2.0, 0.0)]          # grid points: x = (i - 32) * 0.25
+    w = _two_peaks(p, centres, amps)
+    psi2, a, b = O.dumbbell_order_parameter(w, p, centres, 1.5)
+    assert psi2 == pytest.approx(expect, abs=1e-12)
+    assert a == pytest.approx(amps[0], rel=1e-12) and b == pytest.approx(amps[1], rel=1e-12)
+
+
+def test_dumbbell_region_is_closed_and_excludes_outside_peaks():
+    p = O.Params(n=64, dx=0.25)
+    w = np.zeros((64, 64))
+    w[32, 32 - 8] = 0.5          # (-2, 0): left centre
+    w[32, 32 + 8] = -0.5         # (+2, 0): right centre
+    w[32, 32 - 14] = 5.0         # (-3.5, 0): exactly 1.5 from the left centre -> inside
+    w[32, 32 + 15] = 9.0         # (+3.75, 0): 1.75 from the right centre -> outside
+    psi2, a, b = O.dumbbell_order_parameter(w, p, [(-2.0, 0.0), (2.0, 0.0)], 1.5)
+    assert (a, b) == (5.0, -0.5)
+    assert psi2 == pytest.approx(4.5 / 5.5, abs=1e-15)

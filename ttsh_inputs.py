@@ -70,6 +70,24 @@ def dumbbell_mask(n: int, dx: float, radius: float, distance: float) -> np.ndarr
     return (left & right).astype(np.uint8)
 
 
+def blob_mask(n: int, dx: float, seed: int, lobes: int = 5, obstacle: float = 1.0) -> np.ndarray:
+    """An irregular binary domain: the union of `lobes` discs (centres and radii from
+    SplitMix64 draws) is unmasked, except a masked disc obstacle of radius `obstacle` at the
+    first lobe's centre.  Stands in for the paper's arbitrary-image boundaries."""
+    X, Y = grid_coords(n, dx)
+    L = n * dx
+    u = uniform01(seed, np.arange(3 * lobes))
+    inside = np.zeros((n, n), dtype=bool)
+    for i in range(lobes):
+        cx, cy = (u[3 * i] - 0.5) * 0.3 * L, (u[3 * i + 1] - 0.5) * 0.3 * L
+        r = (0.12 + 0.08 * u[3 * i + 2]) * L
+        inside |= (X - cx) ** 2 + (Y - cy) ** 2 < r * r
+        if i == 0:
+            ox, oy = cx, cy
+    inside &= (X - ox) ** 2 + (Y - oy) ** 2 >= obstacle * obstacle
+    return (~inside).astype(np.uint8)
+
+
 def noise_velocity(mask: np.ndarray, seed: int, amplitude: float = 0.01):
     """Uniform noise U[-A, A) for (v_x, v_y) at unmasked points (mask == 0), zero elsewhere."""
     n = mask.shape[0]
