@@ -129,16 +129,28 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, n, precision):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels."""
+def plan_variant(kernel, plan):
+    if kernel == "row_pass":
+        return [plan["rows_per_block"], plan["row_points_per_thread"]]
+    return [plan["col_points_per_thread"]]
+
+
+def profile_record(fname, key, kernel, n, precision, plan):
+    """A per-launch counter from a committed ncu summary, if it was taken on the current
+    kernel sources and on the tile variant the autotuner chose."""
     try:
-        t = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        t = json.load(open(os.path.join(ROOT, "profiles", fname)))
         e = t[f"{kernel}:{n}:{precision}"]
-        if e.get("csrc_hash") == csrc_hash():
-            return float(e["dram_bytes_per_launch"])
+        if e.get("csrc_hash") == csrc_hash() and list(e["variant"]) == plan_variant(kernel, plan):
+            return float(e[key])
     except Exception:
         pass
     return None
+
+
+def ncu_traffic(kernel, n, precision, plan):
+    """DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)."""
+    return profile_record("traffic.json", "dram_bytes_per_launch", kernel, n, precision, plan)
 
 
 def algorithmic_bytes(n, elt):
@@ -149,6 +161,30 @@ def algorithmic_bytes(n, elt):
     row = 4 * H * n * c + n * n * elt + 3 * H * n * c
     col = 3 * H * n * c + 2 * H * NK * c + 4 * H * n * c
     return {"row_pass": row, "col_pass": col}
+
+
+def algorithmic_flops(n):
+    """Nominal flops of one launch of each pass: an m-point complex transform counts
+    5 m log2 m (the radix-2 convention); a real row transform of length n is an n/2-point
+    complex transform plus a 12-flop (inverse) or 14-flop (forward, kept outputs only)
+    twiddle pass; 15 flops per point of real-space terms; 30 flops per stored mode of
+    spectral update and multipliers."""
+    L, H, NK = n // 2, n // 4 + 1, n // 2 + 1
+    fft = lambda m: 5.0 * m * np.log2(m)
+    row = n * (5 * (fft(L) + 12 * L) + 3 * fft(L) + 3 * 14 * H + 15 * n)
+    col = H * (7 * fft(n) + 30 * NK)
+    return {"row_pass": row, "col_pass": col}
+
+
+# one DFMA per clock per SM partition pair: 2 DFMA/clk/SM x 2 flops x 152 SMs x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# 128 FP32 lanes/SM x 2 flops x 152 SMs x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def ncu_executed(kernel, n, precision, plan):
+    """Executed floating-point operations per launch (ncu FMA x 2 + ADD + MUL instruction counts)."""
+    return profile_record("flops.json", "executed_flops_per_launch", kernel, n, precision, plan)
 
 
 # ----------------------------------------------------------------------- CPU oracle leg
@@ -257,9 +293,20 @@ def run_ours(args, rank, world, local_rank):
         r64, c64 = d64.time_kernels(max(20, iters // 4))
         d64.close()
         v64 = world * n * n * S64 * K / t64
+        fl = algorithmic_flops(n)
+        k64 = "row_pass" if r64 >= c64 else "col_pass"
+        ms64 = max(r64, c64)
+        ach64 = fl[k64] / (ms64 * 1e-3) / 1e12
+        ex64 = ncu_executed(k64, n, 64, plan64)
         fp64 = {"value": v64, "unit": UNIT, "solver_steps_per_step": S64,
                 "ms_per_solver_step": 1e3 * t64 / (S64 * K), "row_pass_ms": r64, "col_pass_ms": c64,
-                "fp32_over_fp64": value / v64, "plan": plan64}
+                "fp32_over_fp64": value / v64, "plan": plan64,
+                "roofline": {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": ncu_traffic(k64, n, 64, plan64),
+                             "kernel": k64, "kernel_ms": ms64, "algorithmic_flops": fl[k64],
+                             "executed_flops": ex64,
+                             "executed_tflops": None if ex64 is None else ex64 / (ms64 * 1e-3) / 1e12,
+                             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (nominal FP64 rate)"}}
 
     # ---- batched sweep: 48 domains (128^2..512^2 circles and dumbbells) in lock step ----
     batched = None
@@ -355,12 +402,19 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_src = peaks()
     achieved = ab[dom_k] / (dom_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": ncu_traffic(dom_k, n, 32),
+                "frac": achieved / peak, "traffic": ncu_traffic(dom_k, n, 32, plan32),
                 "kernel": dom_k, "kernel_ms": dom_ms, "algorithmic_bytes": ab[dom_k],
                 "peak_source": f"{peak_src} (copy bandwidth)",
                 "passes_ms": {"row_pass": row_ms, "col_pass": col_ms},
                 "share": {"row_pass": row_ms / (row_ms + col_ms), "col_pass": col_ms / (row_ms + col_ms)},
                 "step_bytes_per_point": (ab["row_pass"] + ab["col_pass"]) / (n * n)}
+    fl32 = algorithmic_flops(n)
+    roofline["alu_context"] = {"achieved_tflops": fl32[dom_k] / (dom_ms * 1e-3) / 1e12,
+                               "peak_tflops": FP32_PEAK_TFLOPS,
+                               "frac": fl32[dom_k] / (dom_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                               "algorithmic_flops": fl32[dom_k],
+                               "executed_flops": ncu_executed(dom_k, n, 32, plan32),
+                               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
