@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="circle512", choices=sorted(ti.WORKLOADS))
     ap.add_argument("--solver-steps", type=int, default=None)
+    ap.add_argument("--record-every", type=int, default=10,
+                    help="time-series sample interval in solver steps (0: plain stepping)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -189,7 +191,7 @@ def ncu_executed(kernel, n, precision, plan):
 
 # ----------------------------------------------------------------------- CPU oracle leg
 
-def time_oracle(w, budget_s=10.0, min_steps=3):
+def time_oracle(w, record_every, budget_s=10.0, min_steps=3):
     from oracle import ttsh_oracle as O
     n, dx = w["n"], w["dx"]
     mask = ti.circle_mask(n, dx, w["radius"])
@@ -200,6 +202,8 @@ def time_oracle(w, budget_s=10.0, min_steps=3):
     s = O.step(s, K, p)   # warm
     steps, t0 = 0, time.perf_counter()
     while steps < min_steps or time.perf_counter() - t0 < budget_s:
+        if record_every > 0 and steps % record_every == 0:
+            O.diagnostics(s, p)
         s = O.step(s, K, p)
         steps += 1
     dt = time.perf_counter() - t0
@@ -234,14 +238,26 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
-    def timed_segments(dom, nseg, steps_per):
+    RE = args.record_every
+    cap = -(-S // RE) if RE > 0 else 0
+    series = torch.zeros(max(cap, 1) * 5, dtype=torch.float64, device=dev)
+
+    def advance(dom, steps_per, record=True):
+        """One timed step's work: steps_per solver steps, recording energy, enstrophy and the
+        order parameter every RE steps on the device (the workload's time series)."""
+        if record and RE > 0:
+            dom.step_record(steps_per, RE, series.data_ptr(), cap)
+        else:
+            dom.step(steps_per)
+
+    def timed_segments(dom, nseg, steps_per, record=True):
         evs = []
         for i in range(nseg):
             with torch.cuda.stream(stream):
                 flush.fill_(float(i))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            dom.step(steps_per)
+            advance(dom, steps_per, record)
             e1.record(stream)
             evs.append((e0, e1))
         stream.synchronize()
@@ -259,7 +275,7 @@ def run_ours(args, rank, world, local_rank):
     dom.set_velocity(vx0, vy0)
     plan32 = dom.autotune(iters=max(20, min(400, int(4e7 // (n * n)))))   # untimed
     for _ in range(W):
-        dom.step(S)
+        advance(dom, S)
     dom.synchronize()
     torch.cuda.synchronize()
     barrier()
@@ -272,6 +288,9 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     t32 = max_over_ranks(t32)
     value = world * n * n * S * K / t32
+    series_last = series[: cap * 5].view(-1, 5)[-1].tolist() if cap > 0 else None
+    # the same steps without the time series, for context (untimed by the headline)
+    t_plain = max_over_ranks(timed_segments(dom, K, S, record=False))
 
     # kernel-level timing for the roofline (same domain, same stream; state restored)
     iters = max(50, min(2000, int(2e7 // (n * n))))
@@ -286,7 +305,7 @@ def run_ours(args, rank, world, local_rank):
         d64.set_velocity(vx0, vy0)
         plan64 = d64.autotune(iters=max(10, min(100, int(1e7 // (n * n)))))
         S64 = max(1, S // 4)
-        d64.step(S64)
+        advance(d64, S64)
         d64.synchronize()
         barrier()
         t64 = max_over_ranks(timed_segments(d64, K, S64))
@@ -374,9 +393,16 @@ def run_ours(args, rank, world, local_rank):
         lib = ttsh.load_library()
         P = lambda a: a.ctypes.data_as(ttsh._D)
 
+        hser = torch.empty(max(cap, 1) * 5, dtype=torch.float64, pin_memory=True)
+
         def e2e_step():
             ttsh._check(lib.ttsh_set_velocity(de.h, P(hx), P(hy)))
-            ttsh._check(lib.ttsh_step(de.h, S))
+            if RE > 0:
+                ttsh._check(lib.ttsh_step_record(de.h, S, RE, series.data_ptr(), cap, None))
+                with torch.cuda.stream(stream):
+                    hser.copy_(series, non_blocking=True)
+            else:
+                ttsh._check(lib.ttsh_step(de.h, S))
             ttsh._check(lib.ttsh_get_fields(de.h, P(ox), P(oy), P(ow)))
 
         e2e_step()
@@ -387,7 +413,10 @@ def run_ours(args, rank, world, local_rank):
         te = max_over_ranks(time.perf_counter() - t0)
         de.close()
         e2e = {"value": world * n * n * S * K / te, "unit": UNIT,
-               "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": 3 * n * n * 8}
+               "h2d_bytes_per_step": 2 * n * n * 8,
+               "d2h_bytes_per_step": 3 * n * n * 8 + (cap * 5 * 8 if RE > 0 else 0),
+               "path": "ttsh_set_velocity (pinned host) + ttsh_step_record + time series and "
+                       "ttsh_get_fields to pinned host, wall clock"}
 
     if dist:
         torch.distributed.destroy_process_group()
@@ -418,9 +447,10 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, steps, dt = time_oracle(w)
+        v, steps, dt = time_oracle(w, RE)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{steps} oracle (numpy FP64, single-threaded) steps of the same {n}x{n} workload in {dt:.1f} s"}
+               "sample": f"{steps} oracle (numpy FP64, single-threaded) steps of the same {n}x{n} workload in "
+                         f"{dt:.1f} s, oracle diagnostics every {RE} steps"}
 
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -429,8 +459,12 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": workload_desc(args.workload, w, S), "n": n, "dx": dx,
                    "radius": w["radius"], "solver_steps_per_step": S, "plan": plan32,
                    "l2": "flushed (256 MiB write) before every timed step; the state stays L2-resident within a step",
+                   "time_series": (f"energy, enstrophy, psi recorded on the device every {RE} solver steps "
+                                   f"({cap} samples per timed step, ttsh_step_record)") if RE > 0 else "none",
                    "parallelism": "replicas" if world == 1 else f"independent domains x{world}"},
-        "e2e": e2e, "gpu_launches": 2 * S * K, "clocks": clk, "roofline": roofline,
+        "e2e": e2e, "gpu_launches": K * (2 * S + (cap + 1 if RE > 0 else 0)), "clocks": clk, "roofline": roofline,
+        "value_without_time_series": world * n * n * S * K / t_plain,
+        "time_series_last_sample": series_last,
         "cpu_baseline": cpu, "fp64": fp64, "batched": batched, "surrogate": surrogate,
         "diagnostics_after": {"energy": diag["energy"], "psi": diag["psi"], "nonfinite": diag["nonfinite"]},
         "ms_per_solver_step": 1e3 * t32 / (K * S),
@@ -449,11 +483,23 @@ def run_reference(args, rank, world):
     K_ = O.process_mask(mask)
     s = O.project_velocity(vx, vy, p)
     S_ref = max(1, int(2.0e6 // (n * n)))   # ~1 s of oracle work per step at 512^2
+    RE = args.record_every
+    count = 0
+
+    def segment(s, count):
+        series = []
+        for _ in range(S_ref):
+            if RE > 0 and count % RE == 0:
+                series.append(O.diagnostics(s, p))
+            s = O.step(s, K_, p)
+            count += 1
+        return s, count
+
     for _ in range(args.warmup):
-        s = O.run(s, K_, p, S_ref)
+        s, count = segment(s, count)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        s = O.run(s, K_, p, S_ref)
+        s, count = segment(s, count)
     dt = time.perf_counter() - t0
     v = n * n * S_ref * args.steps / dt
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
@@ -461,7 +507,8 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, w, S_ref), "n": n,
-                       "solver_steps_per_step": S_ref, "parallelism": "replicas"},
+                       "solver_steps_per_step": S_ref, "parallelism": "replicas",
+                       "time_series": f"oracle diagnostics every {RE} solver steps" if RE > 0 else "none"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{S_ref * args.steps} oracle steps of the {n}x{n} workload"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -148,6 +148,27 @@ ttsh_status ttsh_set_spectral_state(ttsh_domain* d, const double* w_hat, const d
 ttsh_status ttsh_diagnostics(ttsh_domain* d, ttsh_diag* out, double* spectrum, int32_t nbins,
                              const double* centre);
 
+/* Advance nsteps steps (as ttsh_step) while recording a time series of the observables of
+ * Sec. III.C without synchronising: the state at step counts s0, s0 + every, s0 + 2 every,
+ * ... (s0 = step count at the call; one sample per started block of `every` steps, so
+ * ceil(nsteps / every) samples) is sampled inside that step's row pass, which already holds
+ * omega, v_x and v_y in real space.  Sample j is written to series[5 j .. 5 j + 4] =
+ * {step count, energy, enstrophy, psi, number of non-finite points}, with the definitions of
+ * ttsh_diag; per-thread partial sums are taken in the domain precision and combined in
+ * double in a fixed order (repeatable bits).  To record the state after the last step, call
+ * ttsh_diagnostics afterwards.
+ *   every     >= 1 steps between samples.
+ *   series    device (or managed) memory of at least 5 * capacity doubles, owned by the
+ *             caller; it must stay valid until the stream has passed the call.
+ *   capacity  samples series can hold; smaller than ceil(nsteps / every) -> TTSH_E_INVALID
+ *             (nothing is stepped).
+ *   centre    (x, y) for psi, NULL = (0, 0).
+ * Asynchronous on the domain's stream; replayed as CUDA graphs of every * floor(64 / every)
+ * steps when every <= 64.  The paper has no counterpart of this entry point: it is the
+ * device-side form of the energy / order-parameter time series its runs record. */
+ttsh_status ttsh_step_record(ttsh_domain* d, int64_t nsteps, int32_t every, double* series,
+                             int64_t capacity, const double* centre);
+
 /* Kernel timing for roofline reports: records `iters` back-to-back launches of the row pass
  * (then of the column pass) of the current plan as CUDA graphs, replays them between CUDA
  * events on the domain's stream and writes the mean duration of one launch in milliseconds

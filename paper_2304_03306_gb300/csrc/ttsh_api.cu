@@ -46,7 +46,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 struct Layout {
-  size_t what, vmean, K, G, Rr, tw, real, part, colhist, bad, out, save, total;
+  size_t what, vmean, K, G, Rr, tw, real, part, colhist, bad, out, save, rec, recctl, total;
 };
 
 Layout layout_for(int n, size_t elt) {
@@ -71,6 +71,9 @@ Layout layout_for(int n, size_t elt) {
   L.bad = take(64);
   L.out = take((8 + M + 1) * sizeof(double));
   L.save = take(H * NK * 2 * elt + 64);   // state copy kept by ttsh_time_kernels
+  L.rec = take((size_t)n * ttsh::kDiagQ * sizeof(double));   // time-series partials (<= n row blocks)
+  L.recctl = take(64);                                        // time-series write position
+  static_assert(sizeof(ttsh::RecCtl) <= 64, "RecCtl must fit its region");
   L.total = off;
   return L;
 }
@@ -129,6 +132,12 @@ struct ttsh_domain {
   double* psd_omega = nullptr;   // nfreq angular frequencies
   double2* psd_acc = nullptr;    // [2][nfreq][H*NK]: sums with exp(-i W t) and exp(+i W t)
   double* psd_S = nullptr;       // nfreq results
+  // time-series recording (ttsh_step_record): cached graph of `rec_len` steps with a sample
+  // every `rec_every` steps, valid for the centre and plan below (the destination is read
+  // from device memory set at each call)
+  cudaGraphExec_t rec_graph = nullptr;
+  int rec_len = 0, rec_every = 0, rec_rv = -1, rec_cv = -1;
+  double rec_cx = 0.0, rec_cy = 0.0;
 };
 
 namespace {
@@ -296,6 +305,18 @@ cudaError_t launch_spectrum_reduce(const double* colhist, int ncols, int nbins, 
                                    double* out, cudaStream_t s) {
   spectrum_reduce_kernel<<<(nbins + 127) / 128, 128, 0, s>>>(colhist, ncols, nbins, scale, out);
   return cudaGetLastError();
+}
+
+__global__ void record_begin_kernel(RecCtl* c, long long base, double* series, long long capacity,
+                                    int every, int nblocks, double inv2n2) {
+  c->count = 0;
+  c->base = base;
+  c->series = series;
+  c->capacity = capacity;
+  c->every = every;
+  c->nblocks = nblocks;
+  c->inv2n2 = inv2n2;
+  c->overflow = 0;
 }
 
 }  // namespace ttsh
@@ -509,6 +530,57 @@ ttsh_status batch_build_graph(ttsh_batch* b) {
 
 }  // namespace
 
+namespace {
+
+// One step whose row pass also writes the time-series partials; an extra block of its column
+// pass appends the sample.
+ttsh_status record_step(ttsh_domain* d, cudaStream_t s) {
+  char* base = static_cast<char*>(d->ws);
+  ttsh::DomainDev dv = d->dev;
+  dv.rec = reinterpret_cast<double*>(base + d->lay.rec);
+  dv.recctl = base + d->lay.recctl;
+  dv.cx = d->rec_cx;
+  dv.cy = d->rec_cy;
+  cudaError_t e = d->ops.row_step[d->rv].fn(dv, s);
+  if (e != cudaSuccess) return cuda_fail(e, "recorded row pass launch");
+  e = d->ops.col_step[d->cv].fn(dv, s);
+  if (e != cudaSuccess) return cuda_fail(e, "recorded column pass launch");
+  return TTSH_OK;
+}
+
+void drop_record_graph(ttsh_domain* d) {
+  if (d->rec_graph) cudaGraphExecDestroy(d->rec_graph);
+  d->rec_graph = nullptr;
+  d->rec_len = 0;
+}
+
+// Graph of rec_len = every * floor(kGraphLen / every) steps with a sample at every
+// `every`-th step, starting with one.
+ttsh_status build_record_graph(ttsh_domain* d) {
+  const int len = d->rec_every * (kGraphLen / d->rec_every);
+  TTSH_CUDA(cudaStreamBeginCapture(d->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+  ttsh_status st = TTSH_OK;
+  for (int i = 0; i < len && st == TTSH_OK; ++i)
+    st = (i % d->rec_every == 0) ? record_step(d, d->capture) : one_step(d, d->capture);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(d->capture, &g);
+  if (st != TTSH_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "end capture");
+  e = cudaGraphInstantiate(&d->rec_graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    d->rec_graph = nullptr;
+    return cuda_fail(e, "graph instantiate");
+  }
+  d->rec_len = len;
+  return TTSH_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void ttsh_default_params(ttsh_params* p) {
@@ -643,6 +715,7 @@ void ttsh_destroy_domain(ttsh_domain* d) {
   if (d->psd_acc) cudaFree(d->psd_acc);
   if (d->psd_S) cudaFree(d->psd_S);
   if (d->graph) cudaGraphExecDestroy(d->graph);
+  if (d->rec_graph) cudaGraphExecDestroy(d->rec_graph);
   if (d->capture) cudaStreamDestroy(d->capture);
   if (d->owns_ws && d->ws) cudaFree(d->ws);
   delete d;
@@ -691,6 +764,67 @@ ttsh_status ttsh_step(ttsh_domain* d, int64_t nsteps) {
   }
   for (; left > 0; --left) {
     if ((st = one_step(d, d->stream)) != TTSH_OK) return st;
+    d->steps += 1;
+  }
+  return TTSH_OK;
+}
+
+ttsh_status ttsh_step_record(ttsh_domain* d, int64_t nsteps, int32_t every, double* series,
+                             int64_t capacity, const double* centre) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  if (nsteps < 0) return fail(TTSH_E_INVALID, "nsteps must be >= 0");
+  if (every < 1) return fail(TTSH_E_INVALID, "every must be >= 1");
+  const int64_t nsamp = (nsteps + every - 1) / every;
+  if (nsamp > 0 && !series) return fail(TTSH_E_INVALID, "series is NULL");
+  if (capacity < nsamp) return fail(TTSH_E_INVALID, "capacity is smaller than the number of samples");
+  if (nsamp > 0) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, series) != cudaSuccess ||
+        (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();
+      return fail(TTSH_E_INVALID, "series must be device (or managed) memory");
+    }
+  }
+  const double cx = centre ? centre[0] : 0.0, cy = centre ? centre[1] : 0.0;
+  if (!std::isfinite(cx) || !std::isfinite(cy)) return fail(TTSH_E_INVALID, "centre must be finite");
+  if (d->rec_graph && (d->rec_every != every || d->rec_cx != cx || d->rec_cy != cy || d->rec_rv != d->rv ||
+                       d->rec_cv != d->cv))
+    drop_record_graph(d);
+  d->rec_every = every;
+  d->rec_cx = cx;
+  d->rec_cy = cy;
+  d->rec_rv = d->rv;
+  d->rec_cv = d->cv;
+  cudaStream_t s = d->stream;
+  char* base = static_cast<char*>(d->ws);
+  ttsh::record_begin_kernel<<<1, 1, 0, s>>>(reinterpret_cast<ttsh::RecCtl*>(base + d->lay.recctl), (long long)d->steps,
+                                            series, capacity, every, d->n / d->ops.row_step[d->rv].rows,
+                                            1.0 / (2.0 * (double)d->n * (double)d->n));
+  TTSH_CUDA(cudaGetLastError(), "time-series start");
+  ttsh_status st;
+  int64_t i = 0;
+  while (i < nsteps) {
+    if (i % every == 0) {
+      if (every <= kGraphLen && i > 0 && nsteps - i >= every * (kGraphLen / every)) {
+        // the first sample of the call ran eagerly, so the kernels' attributes are set
+        if (!d->rec_graph && (st = build_record_graph(d)) != TTSH_OK) return st;
+        TTSH_CUDA(cudaGraphLaunch(d->rec_graph, s), "graph launch");
+        i += d->rec_len;
+        d->steps += d->rec_len;
+        continue;
+      }
+      if ((st = record_step(d, s)) != TTSH_OK) return st;
+      ++i;
+      d->steps += 1;
+      if (every > kGraphLen) {   // the plain steps up to the next sample
+        const int64_t k = std::min<int64_t>(every - 1, nsteps - i);
+        if ((st = ttsh_step(d, k)) != TTSH_OK) return st;
+        i += k;
+      }
+      continue;
+    }
+    if ((st = one_step(d, s)) != TTSH_OK) return st;
+    ++i;
     d->steps += 1;
   }
   return TTSH_OK;
@@ -875,6 +1009,7 @@ ttsh_status ttsh_set_plan(ttsh_domain* d, int32_t row_variant, int32_t col_varia
       d->graph = nullptr;
       d->graph_len = 0;
     }
+    drop_record_graph(d);
     d->rv = row_variant;
     d->cv = col_variant;
   }

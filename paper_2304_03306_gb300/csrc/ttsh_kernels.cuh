@@ -33,6 +33,20 @@ namespace ttsh {
 // ---------------------------------------------------------------------------------------
 // Arguments (all device pointers belong to one domain's workspace)
 // ---------------------------------------------------------------------------------------
+// Write position and destination of the time series recorded by ttsh_step_record (set at the
+// start of each call; the column pass of a recorded step appends one sample).
+struct RecCtl {
+  long long count;      // samples written in the current call
+  long long base;       // step count of the first sample
+  double* series;       // destination, 5 doubles per sample
+  long long capacity;   // samples that fit
+  double inv2n2;        // 1 / (2 N^2)
+  int every;            // steps between samples
+  int nblocks;          // row blocks whose partials make one sample
+  int overflow;         // a sample did not fit (the host rejects such calls up front)
+  int pad;
+};
+
 template <typename T>
 struct Args {
   cplx<T>* what;        // state omega^, [mx][j], H x NK
@@ -43,6 +57,8 @@ struct Args {
   const cplx<T>* tw;    // W_N^m, m in [0, N)
   double* real;         // double staging, [3][N][N]
   double* part;         // per-block diagnostic partial sums
+  double* rec;          // per-block time-series partials of a recorded step, or null
+  RecCtl* recctl;       // with rec: where the column pass appends the step's sample
   T a, b, lam, gv, gw, dt, dk, mean_decay;   // mean_decay = exp((a - 1) dt)
   double dx, cx, cy;    // grid spacing and the psi centre
 };
@@ -53,6 +69,7 @@ enum ColMode { COL_STEP = 0, COL_PROLOGUE = 1, COL_PROJECT = 2, COL_MASK = 3, CO
 
 constexpr int kDiagQ = 5;   // per-block partials: sum|v|^2, sum w^2, sum|e_th.v|, sum|v|, #nonfinite
 constexpr int kSmemLimit = 220 * 1024;
+constexpr int kRecSmem = 32 * kDiagQ * 8;   // static shared memory of the time-series reduction
 
 __host__ __device__ constexpr int align16(int v) { return (v + 15) / 16 * 16; }
 
@@ -111,7 +128,8 @@ struct RowGeo {
   static constexpr int NT = cmax(64, cmin(1024, F * R * TT));
   static constexpr int SEG = R * CB;                        // bytes per (plane, mx) segment
   static constexpr int CHUNK = SEG % 16 == 0 ? 16 : 8;
-  static constexpr bool VALID = SMEM <= 227 * 1024 && N % R == 0 && R <= N && TT <= 1024 && NT % TT == 0;
+  static constexpr bool VALID = SMEM + (KIND == ROW_STEP ? kRecSmem : 0) <= 227 * 1024 && N % R == 0 &&
+                                R <= N && TT <= 1024 && NT % TT == 0;
 };
 
 // Column-pass geometry and shared-memory plan.
@@ -141,6 +159,89 @@ struct ColGeo {
   static constexpr int NT = cmax(64, cmin(1024, FB * TT));
   static constexpr bool VALID = SMEM <= 227 * 1024 && TT <= 1024 && NT % TT == 0;
 };
+
+// ---------------------------------------------------------------------------------------
+// Time-series sample taken inside a step's row pass.  The pass already holds omega, v_x and
+// v_y of its R rows in real space (the state the step starts from), so the energy,
+// enstrophy and order-parameter sums cost one extra sweep over shared memory: per-thread
+// sums in T over the thread's points, then a fixed-order reduction in double (shuffles
+// inside a warp, warps in index order) to kDiagQ partials per block, written to A.rec.
+// Same quantities as ROW_INV_DIAG: sum |v|^2, sum omega^2, sum |e_theta . v| (e_theta = 0 at
+// the centre), sum |v|, number of points with a non-finite value.
+// ---------------------------------------------------------------------------------------
+template <typename T, int N, int R, int NT, typename RL>
+__device__ __forceinline__ void record_partials(const Args<T>& A, int blk, int y0, RL rl) {
+  const T dx = (T)A.dx, cx = (T)A.cx, cy = (T)A.cy;
+  T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  int bad = 0;
+  for (int e = threadIdx.x; e < R * N; e += NT) {
+    const int r = e / N, x = e % N;
+    const T w = rl(0, r, x), vx = rl(3, r, x), vy = rl(4, r, x);
+    const T px = (T)(x - N / 2) * dx - cx;
+    const T py = (T)(y0 + r - N / 2) * dx - cy;
+    const T rr2 = px * px + py * py;
+    const T v2 = vx * vx + vy * vy;
+    s0 += v2;
+    s1 += w * w;
+    s2 += rr2 > (T)0 ? fabs(px * vy - py * vx) * rsqrt(rr2) : (T)0;
+    s3 += sqrt(v2);
+    bad += (isfinite(w) && isfinite(vx) && isfinite(vy)) ? 0 : 1;
+  }
+  double q[kDiagQ] = {(double)s0, (double)s1, (double)s2, (double)s3, (double)bad};
+  constexpr int NW = (NT + 31) / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wl = cmin(32, NT - warp * 32);   // lanes present in this warp
+  const unsigned mask = wl == 32 ? 0xffffffffu : ((1u << wl) - 1u);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int k = 0; k < kDiagQ; ++k) {
+      const double o = __shfl_down_sync(mask, q[k], off);
+      if (lane + off < wl) q[k] += o;
+    }
+  }
+  __shared__ double wsum[NW][kDiagQ];
+  if (lane == 0)
+    for (int k = 0; k < kDiagQ; ++k) wsum[warp][k] = q[k];
+  __syncthreads();
+  if (threadIdx.x < kDiagQ) {
+    double t = 0.0;
+    for (int w2 = 0; w2 < NW; ++w2) t += wsum[w2][threadIdx.x];
+    A.rec[(size_t)blk * kDiagQ + threadIdx.x] = t;
+  }
+}
+
+// Finish a recorded step's sample (one extra block of the column pass, which runs beside the
+// column blocks): sum the row blocks' partials in a fixed order (lane-strided, then a shuffle
+// tree in warp 0) and append {step, energy, enstrophy, psi, non-finite count}.
+template <typename T>
+__device__ __forceinline__ void record_sample(const Args<T>& A) {
+  if (threadIdx.x >= 32) return;
+  RecCtl* c = A.recctl;
+  const int lane = threadIdx.x;
+  double q[kDiagQ] = {0, 0, 0, 0, 0};
+  for (int b = lane; b < c->nblocks; b += 32)
+    for (int k = 0; k < kDiagQ; ++k) q[k] += A.rec[(size_t)b * kDiagQ + k];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+    for (int k = 0; k < kDiagQ; ++k) q[k] += __shfl_down_sync(0xffffffffu, q[k], off);
+  if (lane == 0) {
+    const double two_over_pi = 0.63661977236758134307553505349005744813783858296183;
+    const long long i = c->count;
+    if (i < c->capacity) {
+      double* o = c->series + (size_t)i * 5;
+      o[0] = (double)(c->base + i * (long long)c->every);
+      o[1] = q[0] * c->inv2n2;
+      o[2] = q[1] * c->inv2n2;
+      o[3] = (q[2] / q[3] - two_over_pi) / (1.0 - two_over_pi);
+      o[4] = q[4];
+    } else {
+      c->overflow = 1;
+    }
+    c->count = i + 1;
+  }
+}
 
 // ---------------------------------------------------------------------------------------
 // Row pass body (one block = rows [y0, y0 + R))
@@ -230,6 +331,7 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
   };
 
   if constexpr (KIND == ROW_STEP) {
+    if (A.rec != nullptr) record_partials<T, N, R, NT>(A, blk, y0, rl);
     for (int e = tid; e < R * N; e += NT) {
       const int r = e / N, x = e % N;
       const T w = rl(0, r, x), wx = rl(1, r, x), wy = rl(2, r, x);
@@ -495,6 +597,12 @@ template <typename T, int N, int MODE, int PEV>
 __global__ void __launch_bounds__(ColGeo<T, N, MODE, PEV>::NT)
 col_kernel(Args<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if constexpr (MODE == COL_STEP) {
+    if (blockIdx.x == ColGeo<T, N, MODE, PEV>::H) {   // launched only for a recorded step
+      record_sample(A);
+      return;
+    }
+  }
   col_body<T, N, MODE, PEV>(A, blockIdx.x, smem_raw);
 }
 
@@ -521,35 +629,58 @@ col_kernel_batched(const Args<T>* __restrict__ args) {
 // Sum nblocks x kDiagQ partials into out[kDiagQ] with one block of 256 threads.
 __global__ void diag_reduce_kernel(const double* __restrict__ part, int nblocks, double* out);
 
-// Per-column shell spectrum: one thread per stored column, sequential over its modes.
+// Per-column shell spectrum: one thread per (stored column kx, shell s).  Shell s holds the
+// modes with round(|m|) = s, i.e. s^2 - s + 1 <= m^2 <= s^2 + s (s >= 1; s = 0: m = 0), so in
+// column kx its modes are two contiguous ranges of ky (ky >= 0 and ky < 0); each thread sums
+// them in the storage order of the column.  The s = 0 thread of each column also counts the
+// column's non-finite values.
+__device__ __forceinline__ int isqrt_floor(long long v) {
+  if (v <= 0) return 0;
+  long long r = (long long)sqrt((double)v);
+  while (r * r > v) --r;
+  while ((r + 1) * (r + 1) <= v) ++r;
+  return (int)r;
+}
+
 template <typename T, int N>
 __global__ void spectrum_col_kernel(Args<T> A, int nbins, double* __restrict__ colhist,
                                     int* __restrict__ badcount) {
-  constexpr int M = N / 4, H = M + 1, NK = 2 * M + 1;
-  const int kx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (kx >= H) return;
-  double* h = colhist + (size_t)kx * nbins;
-  for (int s = 0; s < nbins; ++s) h[s] = 0.0;
+  constexpr int M = N / 4, NK = 2 * M + 1;
+  const int kx = blockIdx.y;
+  const int sh = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sh >= nbins) return;
+  const cplx<T>* col = A.what + (size_t)kx * NK;
   const double dk = (double)A.dk;
   const double wgt = kx > 0 ? 2.0 : 1.0;   // mx > 0 columns stand for +-mx
-  int bad = 0;
-  for (int j = 0; j < NK; ++j) {
-    const int ky = j <= M ? j : j - NK;
+  auto energy = [&](int ky) {
     const int m2 = kx * kx + ky * ky;
-    const cplx<T> w = A.what[(size_t)kx * NK + j];
-    const double wr = (double)w.x, wi = (double)w.y;
-    if (!isfinite(wr) || !isfinite(wi)) ++bad;
-    double e;
     if (m2 == 0) {
       const double u = (double)A.vmean[0], v = (double)A.vmean[1];
-      e = u * u + v * v;
-    } else {
-      e = (wr * wr + wi * wi) / (dk * dk * (double)m2);
+      return u * u + v * v;
     }
-    const int s = (int)rint(sqrt((double)m2));
-    if (s < nbins) h[s] += wgt * e;
+    const cplx<T> w = col[ky >= 0 ? ky : ky + NK];
+    const double wr = (double)w.x, wi = (double)w.y;
+    return (wr * wr + wi * wi) / (dk * dk * (double)m2);
+  };
+  double h = 0.0;
+  const long long s2 = (long long)sh * sh;
+  const long long lo2 = sh == 0 ? 0 : s2 - sh + 1, hi2 = sh == 0 ? 0 : s2 + sh;   // range of m^2
+  const long long k2 = (long long)kx * kx;
+  if (hi2 >= k2) {
+    const int ylo = lo2 - k2 <= 0 ? 0 : isqrt_floor(lo2 - k2 - 1) + 1;   // smallest ky >= 0 with ky^2 >= lo2 - kx^2
+    const int yhi = isqrt_floor(hi2 - k2 < 0 ? 0 : hi2 - k2);
+    const int top = yhi < M ? yhi : M;
+    for (int ky = ylo; ky <= top; ++ky) h += wgt * energy(ky);
+    const int nlo = ylo > 1 ? ylo : 1;
+    for (int ky = -top; ky <= -nlo; ++ky) h += wgt * energy(ky);
   }
-  if (bad) atomicAdd(badcount, bad);
+  colhist[(size_t)kx * nbins + sh] = h;
+  if (sh == 0) {
+    int bad = 0;
+    for (int j = 0; j < NK; ++j)
+      if (!isfinite((double)col[j].x) || !isfinite((double)col[j].y)) ++bad;
+    if (bad) atomicAdd(badcount, bad);
+  }
 }
 
 __global__ void spectrum_reduce_kernel(const double* __restrict__ colhist, int ncols, int nbins,

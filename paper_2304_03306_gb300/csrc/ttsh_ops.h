@@ -20,6 +20,8 @@ struct DomainDev {
   double* colhist; // H x (N/4 + 1) spectrum partials
   int* bad;        // non-finite counter
   double* out;     // reduced diagnostics (8 doubles) + spectrum bins
+  double* rec;     // time-series partials of a recorded step (null: plain step)
+  void* recctl;    // time-series write position (RecCtl), used with rec
   double a, b, lam, gv, gw, dx, dt;
   double cx, cy;   // centre for the order parameter
   int n;

@@ -22,6 +22,8 @@ static Args<T> make_args(const DomainDev& d) {
   a.tw = static_cast<const cplx<T>*>(d.tw);
   a.real = d.real;
   a.part = d.part;
+  a.rec = d.rec;
+  a.recctl = static_cast<RecCtl*>(d.recctl);
   const double dk = 2.0 * 3.14159265358979323846264338327950288 / ((double)d.n * d.dx);
   a.a = (T)d.a;
   a.b = (T)d.b;
@@ -61,7 +63,9 @@ static cudaError_t launch_col_mode(const DomainDev& d, cudaStream_t s) {
   static std::atomic<int> done{0};
   cudaError_t e = set_smem(col_kernel<T, N, MODE, PE>, Geo::SMEM, done);
   if (e != cudaSuccess) return e;
-  col_kernel<T, N, MODE, PE><<<Geo::H, Geo::NT, Geo::SMEM, s>>>(make_args<T>(d));
+  // a recorded step adds one block that finishes the time-series sample
+  const int extra = (MODE == COL_STEP && d.rec != nullptr) ? 1 : 0;
+  col_kernel<T, N, MODE, PE><<<Geo::H + extra, Geo::NT, Geo::SMEM, s>>>(make_args<T>(d));
   return cudaGetLastError();
 }
 
@@ -99,7 +103,7 @@ static cudaError_t launch_col(int mode, const DomainDev& d, cudaStream_t s) {
 template <typename T, int N>
 static cudaError_t launch_spec(const DomainDev& d, int nbins, cudaStream_t s) {
   constexpr int H = N / 4 + 1;
-  spectrum_col_kernel<T, N><<<(H + 127) / 128, 128, 0, s>>>(make_args<T>(d), nbins, d.colhist, d.bad);
+  spectrum_col_kernel<T, N><<<dim3((nbins + 127) / 128, H), 128, 0, s>>>(make_args<T>(d), nbins, d.colhist, d.bad);
   return cudaGetLastError();
 }
 

@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH):
         "ttsh_set_velocity": (ctypes.c_int, [_P, _D, _D]),
         "ttsh_set_velocity_device": (ctypes.c_int, [_P, _P, _P]),
         "ttsh_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+        "ttsh_step_record": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, ctypes.c_int64, _D]),
         "ttsh_get_fields": (ctypes.c_int, [_P, _D, _D, _D]),
         "ttsh_get_mask": (ctypes.c_int, [_P, _D]),
         "ttsh_get_spectral_state": (ctypes.c_int, [_P, _D, _D]),
@@ -178,6 +179,13 @@ def ttsh_set_velocity_device(h, vx_ptr: int, vy_ptr: int):
 
 def ttsh_step(h, nsteps: int):
     _check(load_library().ttsh_step(h, int(nsteps)))
+
+
+def ttsh_step_record(h, nsteps: int, every: int, series_ptr: int | None, capacity: int, centre=(0.0, 0.0)):
+    """Step and append {step, energy, enstrophy, psi, nonfinite} every `every` steps to the
+    device array at series_ptr (5 * capacity doubles).  Asynchronous."""
+    c = np.ascontiguousarray(centre, dtype=np.float64)
+    _check(load_library().ttsh_step_record(h, int(nsteps), int(every), series_ptr, int(capacity), _dptr(c)))
 
 
 def ttsh_get_fields(h, n: int):
@@ -442,6 +450,19 @@ class Domain:
 
     def step(self, nsteps: int):
         ttsh_step(self.h, nsteps)
+
+    def step_record(self, nsteps: int, every: int, series_ptr: int | None, capacity: int, centre=(0.0, 0.0)):
+        ttsh_step_record(self.h, nsteps, every, series_ptr, capacity, centre)
+
+    def record(self, nsteps: int, every: int, centre=(0.0, 0.0)):
+        """Step nsteps and return the recorded time series as an array of rows
+        (step, energy, enstrophy, psi, nonfinite); device memory from PyTorch."""
+        import torch
+        ns = (int(nsteps) + int(every) - 1) // int(every)
+        buf = torch.zeros(max(ns, 1) * 5, dtype=torch.float64, device="cuda")
+        self.step_record(nsteps, every, buf.data_ptr(), ns, centre)
+        self.synchronize()
+        return buf[: ns * 5].cpu().numpy().reshape(ns, 5)
 
     def fields(self):
         return ttsh_get_fields(self.h, self.n)
