@@ -14,12 +14,15 @@
 // stage hit distinct banks.
 //
 // Twiddles W_N^m = exp(-2 pi i m / N) come from shared memory (the whole table when it fits
-// in 16 KB, else two tables of ~sqrt(N) entries whose product gives W_N^m), filled once per
-// block from a correctly rounded global table; no stage waits on global memory.
+// in 16 KB, else two tables of ~sqrt(N) entries whose product gives W_N^m; per-stage tables
+// when they fit in 32 KB), copied asynchronously once per block from a correctly rounded
+// global table together with the block's other inputs; no stage waits on global memory.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 namespace ttsh {
 
@@ -110,42 +113,6 @@ __device__ __forceinline__ void dft_reg(cplx<T>* v) {
   }
 }
 
-// Twiddle table in shared memory for W_TWN^m, m in [0, TWN): the full table when it takes at
-// most 16 KB, otherwise two levels W^m = W^{(m >> S) 2^S} * W^{m mod 2^S}.
-template <typename T, int TWN>
-struct TwTab {
-  static constexpr bool FULL = TWN * (int)sizeof(cplx<T>) <= 16384;
-  static constexpr int LOG = ilog2(TWN);
-  static constexpr int SB = FULL ? LOG : (LOG + 1) / 2;
-  static constexpr int NLO = 1 << SB;
-  static constexpr int NHI = TWN >> SB;
-  static constexpr int ENTRIES = NLO + NHI;
-  const cplx<T>* lo;   // W^i,          i < NLO
-  const cplx<T>* hi;   // W^(i * NLO),  i < NHI
-  __device__ __forceinline__ cplx<T> get(int m) const {
-    if constexpr (NHI == 1) {
-      return lo[m];
-    } else {
-      return cmul(hi[m >> SB], lo[m & (NLO - 1)]);
-    }
-  }
-  // Fill from the global table (all threads of the block; caller synchronises).
-  __device__ __forceinline__ static TwTab fill(cplx<T>* sm, const cplx<T>* __restrict__ tw, int tid, int nt) {
-    for (int i = tid; i < ENTRIES; i += nt) sm[i] = i < NLO ? tw[i] : tw[(i - NLO) * NLO];
-    TwTab t;
-    t.lo = sm;
-    t.hi = sm + NLO;
-    return t;
-  }
-};
-
-template <typename T, int DIR, typename TW>
-__device__ __forceinline__ cplx<T> twiddle(const TW& tw, int idx) {
-  cplx<T> w = tw.get(idx);
-  if (DIR > 0) w.y = -w.y;
-  return w;
-}
-
 // Asynchronous global -> shared copies (cp.async, completion tracked per thread).
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -169,6 +136,44 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
 }
 
+// Twiddle table in shared memory for W_TWN^m, m in [0, TWN): the full table when it takes at
+// most 16 KB, otherwise two levels W^m = W^{(m >> S) 2^S} * W^{m mod 2^S}.
+template <typename T, int TWN>
+struct TwTab {
+  static constexpr bool FULL = TWN * (int)sizeof(cplx<T>) <= 16384;
+  static constexpr int LOG = ilog2(TWN);
+  static constexpr int SB = FULL ? LOG : (LOG + 1) / 2;
+  static constexpr int NLO = 1 << SB;
+  static constexpr int NHI = TWN >> SB;
+  static constexpr int ENTRIES = NLO + NHI;
+  const cplx<T>* lo;   // W^i,          i < NLO
+  const cplx<T>* hi;   // W^(i * NLO),  i < NHI
+  __device__ __forceinline__ cplx<T> get(int m) const {
+    if constexpr (NHI == 1) {
+      return lo[m];
+    } else {
+      return cmul(hi[m >> SB], lo[m & (NLO - 1)]);
+    }
+  }
+  // Fill from the global table with cp.async (all threads of the block); the caller waits
+  // (cp_async_wait_all) and synchronises before the first use.
+  __device__ __forceinline__ static TwTab fill(cplx<T>* sm, const cplx<T>* __restrict__ tw, int tid, int nt) {
+    for (int i = tid; i < ENTRIES; i += nt)
+      cp_async<(int)sizeof(cplx<T>)>(sm + i, i < NLO ? tw + i : tw + (size_t)(i - NLO) * NLO);
+    TwTab t;
+    t.lo = sm;
+    t.hi = sm + NLO;
+    return t;
+  }
+};
+
+template <typename T, int DIR, typename TW>
+__device__ __forceinline__ cplx<T> twiddle(const TW& tw, int idx) {
+  cplx<T> w = tw.get(idx);
+  if (DIR > 0) w.y = -w.y;
+  return w;
+}
+
 // Per-stage twiddle tables.  Stage (Ns, R) of a length-L transform multiplies input r of the
 // butterfly with sub-index k by W_TWN^{r k TWN/(Ns R)}; stored as [r - 1][k] (k fastest) those
 // reads are contiguous across a warp, where indexing one W_TWN table with stride r*k would
@@ -186,7 +191,8 @@ struct StageTab {
   static constexpr int ENTRIES = stage_offset(L, PE, L);
   static constexpr bool USE = ENTRIES > 0 && ENTRIES * (int)sizeof(cplx<T>) <= 32768;
   static constexpr int BYTES = USE ? (ENTRIES * (int)sizeof(cplx<T>) + 15) / 16 * 16 : 0;
-  // fill from the global W_TWN table (all threads; caller synchronises)
+  // fill from the global W_TWN table with cp.async (all threads; the caller waits and
+  // synchronises before the first use)
   template <int TWN>
   __device__ __forceinline__ static void fill(cplx<T>* sm, const cplx<T>* __restrict__ tw, int tid, int nt) {
     if constexpr (USE) {
@@ -197,7 +203,7 @@ struct StageTab {
           const int stride = TWN / (Ns * R);
           for (int i = tid; i < (R - 1) * Ns; i += nt) {
             const int r = 1 + i / Ns, k = i % Ns;
-            sm[off + i] = tw[r * k * stride];
+            cp_async<(int)sizeof(cplx<T>)>(sm + off + i, tw + (size_t)r * k * stride);
           }
           off += (R - 1) * Ns;
         }
@@ -206,23 +212,53 @@ struct StageTab {
   }
 };
 
+// Barrier between the stages of one transform.  A transform is owned by TT = L/PE
+// consecutive threads; when TT divides 32 every transform lies inside one warp and touches
+// only its own buffer, so a warp barrier (which also orders the warp's shared-memory
+// accesses) replaces the block barrier.  NT: block size (the last warp may be partial).
+template <int TT, int NT>
+__device__ __forceinline__ void stage_sync() {
+  if constexpr (TT <= 32 && 32 % TT == 0) {
+    constexpr int TAIL = NT % 32;
+    if constexpr (TAIL == 0) {
+      __syncwarp();
+    } else {
+      const int wl = (int)(threadIdx.x >> 5) == NT / 32 ? TAIL : 32;
+      __syncwarp(wl == 32 ? 0xffffffffu : ((1u << wl) - 1u));
+    }
+  } else {
+    __syncthreads();
+  }
+}
+
+// Marker: the first stage reads its inputs from the buffer (no input functor).
+struct NoLoad {};
+
 // One Stockham stage of radix R on a length-L transform at buf (padded), current
-// sub-transform length Ns.  j: this thread's index among the L/PE owners.
-template <typename T, int L, int PE, int R, int Ns, int DIR, int PS, int TWN>
+// sub-transform length Ns.  j: this thread's index among the L/PE owners.  In the first
+// stage (Ns = 1) an input functor ld(bi, m) may supply element m of transform bi instead of
+// the buffer (fusing the caller's pre-pass into the stage); that stage then reads nothing
+// from the buffer, so it needs no barrier between its loads and its stores.
+template <typename T, int L, int PE, int R, int Ns, int DIR, int PS, int TWN, int NT, typename LD>
 __device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
-                                               const TwTab<T, TWN>& tw, const cplx<T>* stab) {
+                                               const TwTab<T, TWN>& tw, const cplx<T>* stab,
+                                               int bi, const LD& ld) {
   constexpr int TT = L / PE;
   constexpr int NB = PE / R;
+  constexpr bool FUSED = Ns == 1 && !std::is_same<LD, NoLoad>::value;
   cplx<T> v[NB][R];
   if (active) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int q = j + b * TT;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = buf[padi<PS>(q + r * (L / R))];
+      for (int r = 0; r < R; ++r) {
+        if constexpr (FUSED) v[b][r] = ld(bi, q + r * (L / R));
+        else v[b][r] = buf[padi<PS>(q + r * (L / R))];
+      }
     }
   }
-  __syncthreads();
+  if constexpr (!FUSED) stage_sync<TT, NT>();
   if (active) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -249,25 +285,29 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
       for (int r = 0; r < R; ++r) buf[padi<PS>(base + r * Ns)] = v[b][bitrev<R>(r)];
     }
   }
-  __syncthreads();
+  stage_sync<TT, NT>();
 }
 
-template <typename T, int L, int PE, int Ns, int DIR, int PS, int TWN>
+template <typename T, int L, int PE, int Ns, int DIR, int PS, int TWN, int NT, typename LD>
 __device__ __forceinline__ void stockham_all(cplx<T>* buf, int j, bool active,
-                                             const TwTab<T, TWN>& tw, const cplx<T>* stab) {
+                                             const TwTab<T, TWN>& tw, const cplx<T>* stab,
+                                             int bi, const LD& ld) {
   if constexpr (Ns < L) {
     constexpr int R = (L / Ns < PE) ? (L / Ns) : PE;
-    stockham_stage<T, L, PE, R, Ns, DIR, PS, TWN>(buf, j, active, tw, stab);
-    stockham_all<T, L, PE, Ns * R, DIR, PS, TWN>(buf, j, active, tw, stab);
+    stockham_stage<T, L, PE, R, Ns, DIR, PS, TWN, NT>(buf, j, active, tw, stab, bi, ld);
+    stockham_all<T, L, PE, Ns * R, DIR, PS, TWN, NT>(buf, j, active, tw, stab, bi, NoLoad{});
   }
 }
 
 // B transforms of length L laid out at sm + b * STRIDE (padded; STRIDE = 0 means the padded
 // length), all threads of the block participate (NT threads).  TWN: length of the twiddle
-// table (a multiple of L); stab: this length's per-stage tables (ignored when unused).
-// Starts and ends with a block barrier.
-template <typename T, int L, int PE, int DIR, int NT, int TWN, int STRIDE = 0>
-__device__ __forceinline__ void fft_batch(cplx<T>* sm, int B, const TwTab<T, TWN>& tw, const cplx<T>* stab) {
+// table (a multiple of L); stab: this length's per-stage tables (ignored when unused);
+// ld: optional input functor ld(b, m) -> element m of transform b (see stockham_stage).
+// Starts with a block barrier and ends with one (the stage barriers in between are warp
+// barriers when every transform lies inside one warp).
+template <typename T, int L, int PE, int DIR, int NT, int TWN, int STRIDE = 0, typename LD = NoLoad>
+__device__ __forceinline__ void fft_batch(cplx<T>* sm, int B, const TwTab<T, TWN>& tw, const cplx<T>* stab,
+                                          const LD& ld = LD{}) {
   constexpr int PS = ilog2(PE);
   constexpr int LP = STRIDE > 0 ? STRIDE : padded_len<L, PS>();
   constexpr int TT = L / PE;
@@ -279,8 +319,9 @@ __device__ __forceinline__ void fft_batch(cplx<T>* sm, int B, const TwTab<T, TWN
   for (int c0 = 0; c0 < B; c0 += PER) {
     const int b = c0 + slot;
     const bool active = b < B;
-    stockham_all<T, L, PE, 1, DIR, PS, TWN>(sm + (active ? b : 0) * LP, j, active, tw, stab);
+    stockham_all<T, L, PE, 1, DIR, PS, TWN, NT>(sm + (active ? b : 0) * LP, j, active, tw, stab, b, ld);
   }
+  if constexpr (TT <= 32 && 32 % TT == 0) __syncthreads();
 }
 
 }  // namespace ttsh

@@ -278,16 +278,16 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
     const char* src = reinterpret_cast<const char*>(A.K + (size_t)y0 * N);
     for (int i = tid; i < NCH; i += NT) cp_async16(reinterpret_cast<char*>(ks) + 16 * i, src + 16 * i);
   }
-  if constexpr (Geo::STAGE_G || Geo::STAGE_K) cp_async_wait_all();
+  cp_async_wait_all();   // tables and staged inputs
   __syncthreads();
 
   // ---- inverse row transforms (C2R through an L-point complex transform) ----
+  // The twiddle pre-pass that turns the half spectrum X of a real row into the L-point
+  // complex input Z[k] = (X[k] + conj X[L-k]) + i conj(W_N^k) (X[k] - conj X[L-k]) is the
+  // input functor of the first transform stage.
   if constexpr (FI > 0) {
-    for (int e = tid; e < FI * R * L; e += NT) {
-      const int r = e % R;
-      const int t = e / R;
-      const int k = t % L;
-      const int f = t / L;
+    auto load = [&](int bt, int k) -> cplx<T> {
+      const int f = bt / R, r = bt % R;
       // spectral source of field f: which G plane and whether to multiply by i kx
       int plane;
       bool dx_mul = false;
@@ -318,9 +318,9 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
       const cplx<T> w = conjg(tw.get(k));        // conj(W_N^k)
       const cplx<T> s = X + conjg(Xm);
       const cplx<T> d = X - conjg(Xm);
-      sm[(f * R + r) * LP + padi<PS>(k)] = s + mul_i(cmul(w, d));
-    }
-    fft_batch<T, L, PE, +1, NT, N, LP>(sm, FI * R, tw, stab);
+      return s + mul_i(cmul(w, d));
+    };
+    fft_batch<T, L, PE, +1, NT, N, LP>(sm, FI * R, tw, stab, load);
   }
 
   // ---- real-space work ----
@@ -544,6 +544,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
       s0[2] = A.vmean[0];
       s0[3] = A.vmean[1];
     }
+    cp_async_wait_all();   // tables
     __syncthreads();
   }
 
@@ -551,9 +552,9 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
   constexpr int NI = Geo::NI;
   for (int f0 = 0; f0 < NI; f0 += FB) {
     const int nb = cmin(FB, NI - f0);
-    for (int e = tid; e < nb * N; e += NT) {
-      const int b = e / N, idx = e % N;
-      const int f = f0 + b;
+    // spectral multipliers of the four fields, applied as the first stage's input functor
+    auto load = [&](int bt, int idx) -> cplx<T> {
+      const int f = f0 + bt;
       const int ky = idx <= N / 2 ? idx : idx - N;
       cplx<T> v = mk<T>(0, 0);
       if (ky >= -M && ky <= M) {
@@ -572,9 +573,9 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
           if (m2 == 0 && f >= 2) v = mk<T>(s0[2 + (f - 2)] * invN, (T)0);   // mean flow
         }
       }
-      buf[b * LP + padi<PS>(idx)] = v;
-    }
-    fft_batch<T, N, PE, +1, NT, N>(buf, nb, tw, stab);
+      return v;
+    };
+    fft_batch<T, N, PE, +1, NT, N, 0>(buf, nb, tw, stab, load);
     for (int e = tid; e < nb * N; e += NT) {
       const int b = e / N, y = e % N;
       A.G[((size_t)(f0 + b) * H + kx) * N + y] = buf[b * LP + padi<PS>(y)];
