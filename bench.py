@@ -156,12 +156,16 @@ def ncu_traffic(kernel, n, precision, plan):
 
 
 def algorithmic_bytes(n, elt):
-    """Bytes one launch of each pass must move (inputs read once, outputs written once)."""
+    """Bytes one launch of each pass must move (inputs read once, outputs written once):
+    the row pass reads the three column-transformed fields (omega, v_x, v_y) on the H = n/4 + 1
+    stored columns and the mask, and writes the three right-hand-side fields on the same
+    columns; the column pass reads those, reads and writes the state column, and writes the
+    three column-transformed fields."""
     H = n // 4 + 1
     NK = n // 2 + 1
     c = 2 * elt
-    row = 4 * H * n * c + n * n * elt + 3 * H * n * c
-    col = 3 * H * n * c + 2 * H * NK * c + 4 * H * n * c
+    row = 3 * H * n * c + n * n * elt + 3 * H * n * c
+    col = 3 * H * n * c + 2 * H * NK * c + 3 * H * n * c
     return {"row_pass": row, "col_pass": col}
 
 
@@ -169,12 +173,13 @@ def algorithmic_flops(n):
     """Nominal flops of one launch of each pass: an m-point complex transform counts
     5 m log2 m (the radix-2 convention); a real row transform of length n is an n/2-point
     complex transform plus a 12-flop (inverse) or 14-flop (forward, kept outputs only)
-    twiddle pass; 15 flops per point of real-space terms; 30 flops per stored mode of
-    spectral update and multipliers."""
+    twiddle pass; 14 flops per point of real-space terms; 30 flops per stored mode of
+    spectral update and multipliers.  Three inverse and three forward transforms per row and
+    per column."""
     L, H, NK = n // 2, n // 4 + 1, n // 2 + 1
     fft = lambda m: 5.0 * m * np.log2(m)
-    row = n * (5 * (fft(L) + 12 * L) + 3 * fft(L) + 3 * 14 * H + 15 * n)
-    col = H * (7 * fft(n) + 30 * NK)
+    row = n * (3 * (fft(L) + 12 * L) + 3 * fft(L) + 3 * 14 * H + 14 * n)
+    col = H * (6 * fft(n) + 30 * NK)
     return {"row_pass": row, "col_pass": col}
 
 

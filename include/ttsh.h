@@ -118,7 +118,10 @@ ttsh_status ttsh_set_velocity(ttsh_domain* d, const double* vx, const double* vy
 ttsh_status ttsh_set_velocity_device(ttsh_domain* d, const double* vx, const double* vy);
 
 /* Advance the state by nsteps steps of Algorithm 1 (Appendix D): real-space nonlinear and
- * mask terms (lines 1-2), DFT of the right-hand side and curl assembly (line 3), the
+ * mask terms (lines 1-2; the advection v.grad(omega) is evaluated in its conservative form
+ * div(v omega), which equals it on every kept mode up to rounding because v and omega are
+ * band-limited to the 1/2-rule disc and div v = 0), DFT of the right-hand side and curl
+ * assembly (line 3), the
  * integrating-factor Euler update (line 4), the k = 0 mean-flow update of Eq. (avg)
  * (lines 6-8), the 1/2-rule dealiasing (lines 9-11), the Hermitian average and the
  * stream-function velocity (lines 13-15).  Asynchronous on the domain's stream; long runs
@@ -201,7 +204,7 @@ ttsh_status ttsh_set_plan(ttsh_domain* d, int32_t row_variant, int32_t col_varia
  *          advanced in place;
  *   v0     v^(0), 2 values, advanced in place.
  * Scratch (inter-pass buffers, twiddle tables) lives in one fixed device array inside the
- * library, sized for n <= 512 (about 7.4 MB, held by every GPU that loads the library until
+ * library, sized for n <= 512 (about 6.4 MB, held by every GPU that loads the library until
  * the process exits); n > 512 -> TTSH_E_INVALID, as are the parameter checks of
  * ttsh_create_domain.  The first call on each device resolves that array's address and
  * writes its twiddle tables (synchronous copies); make that first call before any stream

@@ -61,7 +61,7 @@ Layout layout_for(int n, size_t elt) {
   L.what = take(H * NK * 2 * elt);
   L.vmean = take(64);
   L.K = take(NN * elt);
-  L.G = take(4 * H * n * 2 * elt);
+  L.G = take(3 * H * n * 2 * elt);
   L.Rr = take(3 * H * n * 2 * elt);
   L.tw = take((size_t)n * 2 * elt);
   L.real = take(3 * NN * sizeof(double));

@@ -4,21 +4,31 @@
 // One step of Algorithm 1 (Appendix D) is two fused kernels:
 //
 //   row pass  (one block per R rows of the N x N box, real space)
-//     inverse row transforms of omega^, i kx omega^, i ky omega^, v^x, v^y (column-
-//     transformed by the previous column pass), giving omega, d_x omega, d_y omega, v_x,
-//     v_y (line 2's iDFT[i k omega^] and the ENSURE'd v);
-//     rhs1 = -b |v|^2 v - gamma_v K v, rhs2 = -lambda v.grad(omega) - gamma_w K omega
-//     (lines 1-2); forward row transforms of the three rhs fields, keeping only the
+//     inverse row transforms of omega^, v^x, v^y (column-transformed by the previous column
+//     pass), giving omega, v_x, v_y (the ENSURE'd v); then, per point,
+//       F0 = c1 v_x + lambda v_y omega,  F1 = c1 v_y - lambda v_x omega,  F2 = -gamma_w K omega
+//     with c1 = -b |v|^2 - gamma_v K, and forward row transforms of F0..F2, keeping only the
 //     columns mx <= N/4 that the 1/2 rule can keep.
 //
 //   column pass (one block per stored column mx = 0..N/4, Fourier space)
-//     forward column transforms of the three rhs fields; curl assembly
-//     rhs^ = i(kx R^1y - ky R^1x) + R^2 (line 3); integrating-factor Euler update (line 4);
-//     k = 0: omega^ = 0 and v^(0) <- exp((a-1) dt)(v^(0) + dt R^1(0)) (lines 6-8, Eq. avg);
-//     zero |m|^2 > (N/4)^2 (lines 9-11); Hermitian average (line 13, only the mx = 0
-//     column needs it in half-spectrum storage); then psi^ = omega^/k^2 and v^ =
-//     (i ky psi^, -i kx psi^) (lines 14-15) and the inverse column transforms of the four
-//     fields the next row pass needs.
+//     forward column transforms of F0..F2; curl assembly rhs^ = i(kx F^1 - ky F^0) + F^2
+//     (line 3); integrating-factor Euler update (line 4); k = 0: omega^ = 0 and
+//     v^(0) <- exp((a-1) dt)(v^(0) + dt R^1(0)) with R^1(0) = F^(0) (lines 6-8, Eq. avg);
+//     zero |m|^2 > (N/4)^2 (lines 9-11); Hermitian average (line 13, only the mx = 0 column
+//     needs it in half-spectrum storage); then psi^ = omega^/k^2 and v^ = (i ky psi^,
+//     -i kx psi^) (lines 14-15) and the inverse column transforms of omega^, v^x, v^y.
+//
+// Why this equals lines 1-3: the advection term is taken in conservative form,
+// v.grad(omega) = div(v omega), so i(kx F^1 - ky F^0) + F^2 = i(kx R^1y - ky R^1x)
+// - lambda (i kx DFT[v_x omega] + i ky DFT[v_y omega]) - gamma_w DFT[K omega] = rhs^.  The two
+// forms agree exactly (up to rounding) on every mode the update keeps: v and omega are
+// band-limited to |m| <= N/4, so their grid product has no aliases inside that disc and its
+// DFT there is the exact convolution, and k . v^(m) = 0 for every m (v comes from the stream
+// function; k = 0 for the mean flow), so the convolution of i k omega^ with v^ equals
+// i k times the convolution of omega^ with v^.  The k = 0 values are unchanged too:
+// sum_x v omega = sum_m v^(m) conj(omega^(m)) = sum_m (i ky, -i kx) |omega^|^2 / k^2 = 0 (odd
+// in m, and omega^(0) = 0).  This needs three inverse transforms per row and per column
+// instead of five and four (no separate grad(omega) fields).
 //
 // Inter-pass buffers are column-major, [field][mx][y], so the column pass streams whole
 // columns and the row pass reads/writes R consecutive y per column.  Every global input a
@@ -52,7 +62,7 @@ struct Args {
   cplx<T>* what;        // state omega^, [mx][j], H x NK
   T* vmean;             // v^(0), 2 values
   T* K;                 // processed mask, N x N
-  cplx<T>* G;           // column-pass output / row-pass input, [4][H][N]
+  cplx<T>* G;           // column-pass output / row-pass input, [3][H][N]: omega, v_x, v_y
   cplx<T>* Rr;          // row-pass output / column-pass input, [3][H][N]
   const cplx<T>* tw;    // W_N^m, m in [0, N)
   double* real;         // double staging, [3][N][N]
@@ -74,7 +84,7 @@ constexpr int kRecSmem = 32 * kDiagQ * 8;   // static shared memory of the time-
 __host__ __device__ constexpr int align16(int v) { return (v + 15) / 16 * 16; }
 
 template <int KIND> __host__ __device__ constexpr int row_inv_fields() {
-  return KIND == ROW_STEP ? 5 : KIND == ROW_INV_FIELDS ? 3 : KIND == ROW_INV_DIAG ? 3
+  return KIND == ROW_STEP ? 3 : KIND == ROW_INV_FIELDS ? 3 : KIND == ROW_INV_DIAG ? 3
        : KIND == ROW_INV_MASK ? 1 : 0;
 }
 template <int KIND> __host__ __device__ constexpr int row_fwd_fields() {
@@ -108,14 +118,15 @@ struct RowGeo {
   static constexpr int FI = row_inv_fields<KIND>();
   static constexpr int FF = row_fwd_fields<KIND>();
   static constexpr int F = cmax(FI, FF);
-  static constexpr int NPL = FI == 0 ? 0 : (KIND == ROW_INV_MASK ? 1 : 4);   // G planes read
+  static constexpr int NPL = FI;   // G planes read (field f comes from plane f)
   static constexpr int CB = (int)sizeof(cplx<T>);
   static constexpr int LPR = row_stride(LP, R, CB / 4);
   static constexpr int TW_BYTES = align16(TwTab<T, N>::ENTRIES * CB) + StageTab<T, L, PE>::BYTES;
   static constexpr int OFF_STAB = align16(TwTab<T, N>::ENTRIES * CB);
-  static constexpr int BUF_BYTES = F * R * LPR * CB;
-  static constexpr int GIN_BYTES = NPL * H * R * CB;
-  static constexpr int KS_BYTES = KIND == ROW_STEP ? R * N * (int)sizeof(T) : 0;
+  // every region starts on a 16-byte boundary (16-byte cp.async destinations)
+  static constexpr int BUF_BYTES = align16(F * R * LPR * CB);
+  static constexpr int GIN_BYTES = align16(NPL * H * R * CB);
+  static constexpr int KS_BYTES = KIND == ROW_STEP ? align16(R * N * (int)sizeof(T)) : 0;
   static constexpr int RED_BYTES = KIND == ROW_INV_DIAG ? kDiagQ * 1024 * 8 : 0;
   static constexpr bool STAGE_K = KS_BYTES > 0 && TW_BYTES + BUF_BYTES + KS_BYTES + RED_BYTES <= kSmemLimit;
   static constexpr bool STAGE_G = GIN_BYTES > 0 &&
@@ -130,6 +141,8 @@ struct RowGeo {
   static constexpr int CHUNK = SEG % 16 == 0 ? 16 : 8;
   static constexpr bool VALID = SMEM + (KIND == ROW_STEP ? kRecSmem : 0) <= 227 * 1024 && N % R == 0 &&
                                 R <= N && TT <= 1024 && NT % TT == 0;
+  static_assert(OFF_BUF % 16 == 0 && OFF_GIN % 16 == 0 && OFF_KS % 16 == 0 && OFF_RED % 16 == 0,
+                "row pass shared-memory regions must be 16-byte aligned");
 };
 
 // Column-pass geometry and shared-memory plan.
@@ -141,7 +154,7 @@ struct ColGeo {
   static constexpr int LP = padded_len<N, PS>();
   static constexpr int TT = N / PE;
   static constexpr int NF = MODE == COL_STEP ? 3 : MODE == COL_PROJECT ? 2 : (MODE == COL_MASK || MODE == COL_ADDW) ? 1 : 0;
-  static constexpr int NI = MODE == COL_MASK ? 1 : 4;
+  static constexpr int NI = MODE == COL_MASK ? 1 : 3;
   static constexpr int CB = (int)sizeof(cplx<T>);
   static constexpr int TW_BYTES = align16(TwTab<T, N>::ENTRIES * CB) + StageTab<T, N, PE>::BYTES;
   static constexpr int OFF_STAB = align16(TwTab<T, N>::ENTRIES * CB);
@@ -152,12 +165,14 @@ struct ColGeo {
   static constexpr int FB = (FIXED + FB0 * LP * CB <= kSmemLimit) ? FB0
                           : (FIXED + 2 * LP * CB <= kSmemLimit && FB0 >= 2) ? 2 : 1;
   static constexpr int OFF_BUF = TW_BYTES;
-  static constexpr int OFF_ACC = OFF_BUF + FB * LP * CB;
+  static constexpr int OFF_ACC = OFF_BUF + align16(FB * LP * CB);
   static constexpr int OFF_WS = OFF_ACC + ACC_BYTES;
   static constexpr int OFF_S0 = OFF_WS + WS_BYTES;
   static constexpr int SMEM = OFF_S0 + 64;
   static constexpr int NT = cmax(64, cmin(1024, FB * TT));
   static constexpr bool VALID = SMEM <= 227 * 1024 && TT <= 1024 && NT % TT == 0;
+  static_assert(OFF_BUF % 16 == 0 && OFF_ACC % 16 == 0 && OFF_WS % 16 == 0 && OFF_S0 % 16 == 0,
+                "column pass shared-memory regions must be 16-byte aligned");
 };
 
 // ---------------------------------------------------------------------------------------
@@ -176,7 +191,7 @@ __device__ __forceinline__ void record_partials(const Args<T>& A, int blk, int y
   int bad = 0;
   for (int e = threadIdx.x; e < R * N; e += NT) {
     const int r = e / N, x = e % N;
-    const T w = rl(0, r, x), vx = rl(3, r, x), vy = rl(4, r, x);
+    const T w = rl(0, r, x), vx = rl(1, r, x), vy = rl(2, r, x);
     const T px = (T)(x - N / 2) * dx - cx;
     const T py = (T)(y0 + r - N / 2) * dx - cy;
     const T rr2 = px * px + py * py;
@@ -287,32 +302,17 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
   // input functor of the first transform stage.
   if constexpr (FI > 0) {
     auto load = [&](int bt, int k) -> cplx<T> {
-      const int f = bt / R, r = bt % R;
-      // spectral source of field f: which G plane and whether to multiply by i kx
-      int plane;
-      bool dx_mul = false;
-      if constexpr (KIND == ROW_STEP) {
-        plane = f == 0 ? 0 : f == 1 ? 0 : f - 1;   // w, i kx w, (i ky w), vx, vy
-        dx_mul = (f == 1);
-      } else if constexpr (KIND == ROW_INV_MASK) {
-        plane = 0;
-      } else {
-        plane = f == 0 ? 0 : f + 1;                 // w, vx, vy
-      }
+      const int f = bt / R, r = bt % R;   // field f (omega, v_x, v_y / the mask) from G plane f
       cplx<T> X = mk<T>(0, 0), Xm = mk<T>(0, 0);
       const int km = L - k;
       if constexpr (Geo::STAGE_G) {
-        const cplx<T>* src = gin + (size_t)plane * H * R + r;
+        const cplx<T>* src = gin + (size_t)f * H * R + r;
         if (k <= M) X = src[k * R];
         if (km <= M) Xm = src[km * R];
       } else {
-        const cplx<T>* src = A.G + (size_t)plane * H * N + (y0 + r);
+        const cplx<T>* src = A.G + (size_t)f * H * N + (y0 + r);
         if (k <= M) X = src[(size_t)k * N];
         if (km <= M) Xm = src[(size_t)km * N];
-      }
-      if (dx_mul) {
-        X = mul_i(X) * (A.dk * (T)k);
-        Xm = mul_i(Xm) * (A.dk * (T)km);
       }
       if (k == 0) X.y = 0;   // the mx = 0 entry of a real row is real
       const cplx<T> w = conjg(tw.get(k));        // conj(W_N^k)
@@ -334,16 +334,18 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
     if (A.rec != nullptr) record_partials<T, N, R, NT>(A, blk, y0, rl);
     for (int e = tid; e < R * N; e += NT) {
       const int r = e / N, x = e % N;
-      const T w = rl(0, r, x), wx = rl(1, r, x), wy = rl(2, r, x);
-      const T vx = rl(3, r, x), vy = rl(4, r, x);
+      const T w = rl(0, r, x), vx = rl(1, r, x), vy = rl(2, r, x);
       T Kv;
       if constexpr (Geo::STAGE_K) Kv = ks[e];
       else Kv = A.K[(size_t)(y0 + r) * N + x];
-      const T v2 = vx * vx + vy * vy;
-      const T c1 = -A.b * v2 - A.gv * Kv;               // line 1
-      rl(0, r, x) = c1 * vx;
-      rl(1, r, x) = c1 * vy;
-      rl(2, r, x) = -A.lam * (vx * wx + vy * wy) - A.gw * Kv * w;   // line 2
+      // explicit fused multiply-adds: every kernel instantiation (single and batched) rounds
+      // the same way
+      const T v2 = fma(vx, vx, vy * vy);
+      const T c1 = fma(-A.b, v2, -(A.gv * Kv));        // line 1: rhs1 = c1 v
+      const T lw = A.lam * w;                           // line 2's advection, conservative form
+      rl(0, r, x) = fma(c1, vx, lw * vy);
+      rl(1, r, x) = fma(c1, vy, -(lw * vx));
+      rl(2, r, x) = -(A.gw * Kv) * w;
     }
   } else if constexpr (KIND == ROW_FWD_VEL || KIND == ROW_FWD_MASK) {
     for (int e = tid; e < FF * R * N; e += NT) {
@@ -465,7 +467,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
           if constexpr (MODE == COL_MASK || MODE == COL_ADDW) {
             a = v;
           } else {
-            // f = 0: (rhs1_x | v_x) -> -i ky; f = 1: (rhs1_y | v_y) -> +i kx; f = 2: rhs2 -> 1
+            // f = 0: (F0 | v_x) -> -i ky; f = 1: (F1 | v_y) -> +i kx; f = 2: F2 -> 1
             if (f == 0) a = a - mul_i(v) * kyp;
             else if (f == 1) a = a + mul_i(v) * kxp;
             else a = a + v;
@@ -567,10 +569,9 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
           const T k2 = A.dk * A.dk * (T)m2;
           const T inv = m2 > 0 ? invN / k2 : (T)0;
           if (f == 0) v = w * invN;                       // omega
-          else if (f == 1) v = mul_i(w) * (kyp * invN);   // i ky omega^ -> d_y omega
-          else if (f == 2) v = mul_i(w) * (kyp * inv);    // v^x = i ky psi^   (line 15)
+          else if (f == 1) v = mul_i(w) * (kyp * inv);    // v^x = i ky psi^   (line 15)
           else v = mul_i(w) * (-kxp * inv);               // v^y = -i kx psi^
-          if (m2 == 0 && f >= 2) v = mk<T>(s0[2 + (f - 2)] * invN, (T)0);   // mean flow
+          if (m2 == 0 && f >= 1) v = mk<T>(s0[2 + (f - 1)] * invN, (T)0);   // mean flow
         }
       }
       return v;

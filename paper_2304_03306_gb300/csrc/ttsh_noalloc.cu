@@ -9,7 +9,7 @@
 // caller's device buffers and keeps its only scratch - the two inter-pass buffers of the
 // row/column step and the twiddle tables - in one file-scope device array of fixed size.
 //
-// The array is sized for grids up to kNoAllocMaxN = 512 in double precision (about 7.4 MB);
+// The array is sized for grids up to kNoAllocMaxN = 512 in double precision (about 6.4 MB);
 // every GPU that loads the library holds it until the process exits.  All calls share it:
 // calls that overlap on the GPU (different streams, or different host threads, at the same
 // time) race on it and must be serialised by the caller.  Nothing in it has to start at
@@ -28,7 +28,7 @@ namespace {
 
 constexpr int kNoAllocMaxN = 512;
 constexpr size_t kMaxH = kNoAllocMaxN / 4 + 1;
-constexpr size_t kGBytes = 4 * kMaxH * kNoAllocMaxN * 2 * sizeof(double);
+constexpr size_t kGBytes = 3 * kMaxH * kNoAllocMaxN * 2 * sizeof(double);
 constexpr size_t kRBytes = 3 * kMaxH * kNoAllocMaxN * 2 * sizeof(double);
 // twiddle tables for n = 16, 32, ..., 512: table n starts at entry n - 16
 constexpr size_t kTwEntries = 2 * kNoAllocMaxN - 16;
