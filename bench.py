@@ -394,7 +394,7 @@ def run_ours(args, rank, world, local_rank):
         hx[:], hy[:] = vx0, vy0
         ox, oy, ow = pin((n, n)), pin((n, n)), pin((n, n))
         de = ttsh.Domain(mask, n, dx, precision=32, stream=stream.cuda_stream)
-        de.set_plan(plan32["row_variant"], plan32["col_variant"])
+        de.set_plan(plan32["row_variant"], plan32["col_variant"], plan32["pdl"])
         lib = ttsh.load_library()
         P = lambda a: a.ctypes.data_as(ttsh._D)
 

@@ -175,8 +175,9 @@ ttsh_status ttsh_step_record(ttsh_domain* d, int64_t nsteps, int32_t every, doub
 /* Kernel timing for roofline reports: records `iters` back-to-back launches of the row pass
  * (then of the column pass) of the current plan as CUDA graphs, replays them between CUDA
  * events on the domain's stream and writes the mean duration of one launch in milliseconds
- * to ms[0] (row pass) and ms[1] (column pass).  The spectral state is saved before and
- * restored after, so the domain continues exactly where it was.  Synchronises.
+ * to ms[0] (row pass) and ms[1] (column pass).  The launches are ordinary ones whatever the
+ * domain's launch mode, so each duration is a whole launch.  The spectral state is saved
+ * before and restored after, so the domain continues exactly where it was.  Synchronises.
  * iters must be in [1, 1000000]. */
 ttsh_status ttsh_time_kernels(ttsh_domain* d, int32_t iters, double* ms);
 
@@ -187,11 +188,20 @@ ttsh_status ttsh_time_kernels(ttsh_domain* d, int32_t iters, double* ms);
  * ttsh_autotune times every variant (as ttsh_time_kernels does, `iters` launches each, state
  * restored) and selects the fastest row and column variant.  plan (8 int32, may be NULL):
  * {row variant, column variant, rows per block, row points per thread, column points per
- * thread, number of row variants, number of column variants, 0}.  ttsh_set_plan selects
- * variants by index (TTSH_E_INVALID if out of range). */
+ * thread, number of row variants, number of column variants, launch mode}.  ttsh_set_plan
+ * selects variants by index (TTSH_E_INVALID if out of range).  After choosing the variants
+ * ttsh_autotune also times whole steps (graphs of up to 64 steps, state restored) in both
+ * launch modes and keeps the faster. */
 ttsh_status ttsh_autotune(ttsh_domain* d, int32_t iters, int32_t* plan);
 ttsh_status ttsh_get_plan(ttsh_domain* d, int32_t* plan);
 ttsh_status ttsh_set_plan(ttsh_domain* d, int32_t row_variant, int32_t col_variant);
+
+/* Launch mode of the step kernels: 0 = ordinary stream-ordered launches; 1 = programmatic
+ * dependent launches, where a pass may start (copy its twiddle tables and mask rows) while
+ * the previous pass is still running and waits on the device (griddepcontrol.wait) before it
+ * reads anything that pass wrote.  Results are bit-identical in both modes; other values ->
+ * TTSH_E_INVALID.  The paper has no counterpart: this is a scheduling option. */
+ttsh_status ttsh_set_launch_mode(ttsh_domain* d, int32_t pdl);
 
 /* Advance a caller-owned state by nsteps steps of Algorithm 1 without allocating any device
  * memory (the paper has no counterpart: this is a library convenience).  It is meant for

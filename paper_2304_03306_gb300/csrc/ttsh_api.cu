@@ -202,6 +202,45 @@ ttsh_status time_launches(ttsh_domain* d, ttsh::StepFn fn, int iters, double* ms
   return TTSH_OK;
 }
 
+// Mean duration of one whole step (row pass then column pass of the current plan and launch
+// mode), from CUDA events around replays of a graph of up to 64 steps.  Advances the state:
+// callers save and restore it.
+ttsh_status time_steps(ttsh_domain* d, int iters, double* ms) {
+  ttsh_status st = one_step(d, d->stream);   // sets kernel attributes outside capture
+  if (st != TTSH_OK) return st;
+  const int per = iters < 64 ? iters : 64;
+  const int reps = (iters + per - 1) / per;
+  TTSH_CUDA(cudaStreamSynchronize(d->stream), "timing warm-up");
+  TTSH_CUDA(cudaStreamBeginCapture(d->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
+  for (int i = 0; i < per && st == TTSH_OK; ++i) st = one_step(d, d->capture);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(d->capture, &g);
+  if (st != TTSH_OK || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return st != TTSH_OK ? st : cuda_fail(e2, "timing capture");
+  }
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "timing graph instantiate");
+  cudaEvent_t ev[2];
+  cudaEventCreate(&ev[0]);
+  cudaEventCreate(&ev[1]);
+  e = cudaGraphLaunch(ge, d->stream);   // warm
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], d->stream);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) e = cudaGraphLaunch(ge, d->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[1], d->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d->stream);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  cudaGraphExecDestroy(ge);
+  if (e != cudaSuccess) return cuda_fail(e, "step timing");
+  *ms = (double)t / ((double)reps * per);
+  return TTSH_OK;
+}
+
 // Save / restore the spectral state around timing runs of the column pass.
 ttsh_status save_state(ttsh_domain* d) {
   const size_t wbytes = (size_t)d->H * d->NK * 2 * d->elt;
@@ -956,8 +995,12 @@ ttsh_status ttsh_time_kernels(ttsh_domain* d, int32_t iters, double* ms) {
   if (iters < 1 || iters > 1000000) return fail(TTSH_E_INVALID, "iters must be in [1, 1000000]");
   ttsh_status st = save_state(d);
   if (st != TTSH_OK) return st;
-  if ((st = time_launches(d, d->ops.row_step[d->rv].fn, iters, &ms[0])) != TTSH_OK) return st;
-  if ((st = time_launches(d, d->ops.col_step[d->cv].fn, iters, &ms[1])) != TTSH_OK) return st;
+  const int pdl = d->dev.pdl;
+  d->dev.pdl = 0;   // each launch timed whole, with no overlap from the next one
+  if ((st = time_launches(d, d->ops.row_step[d->rv].fn, iters, &ms[0])) == TTSH_OK)
+    st = time_launches(d, d->ops.col_step[d->cv].fn, iters, &ms[1]);
+  d->dev.pdl = pdl;
+  if (st != TTSH_OK) return st;
   return restore_state(d);
 }
 
@@ -966,6 +1009,8 @@ ttsh_status ttsh_autotune(ttsh_domain* d, int32_t iters, int32_t* plan) {
   if (iters < 1 || iters > 100000) return fail(TTSH_E_INVALID, "iters must be in [1, 100000]");
   ttsh_status st = save_state(d);
   if (st != TTSH_OK) return st;
+  const int pdl0 = d->dev.pdl;
+  d->dev.pdl = 0;   // variants are timed as plain back-to-back launches
   double best = 1e300;
   int br = 0, bc = 0;
   for (int i = 0; i < d->ops.n_row_variants; ++i) {
@@ -979,8 +1024,35 @@ ttsh_status ttsh_autotune(ttsh_domain* d, int32_t iters, int32_t* plan) {
     if ((st = time_launches(d, d->ops.col_step[i].fn, iters, &t)) != TTSH_OK) return st;
     if (t < best) { best = t; bc = i; }
   }
+  d->dev.pdl = pdl0;
   if ((st = restore_state(d)) != TTSH_OK) return st;
-  return ttsh_set_plan(d, br, bc) == TTSH_OK ? ttsh_get_plan(d, plan) : TTSH_E_INVALID;
+  if ((st = ttsh_set_plan(d, br, bc)) != TTSH_OK) return st;
+  // launch mode: whole steps (row then column pass) with and without programmatic
+  // dependent launch; keep the faster
+  double t_mode[2];
+  for (int pdl = 0; pdl < 2; ++pdl) {
+    if ((st = ttsh_set_launch_mode(d, pdl)) != TTSH_OK) return st;
+    if ((st = save_state(d)) != TTSH_OK) return st;
+    if ((st = time_steps(d, iters, &t_mode[pdl])) != TTSH_OK) return st;
+    if ((st = restore_state(d)) != TTSH_OK) return st;
+  }
+  if ((st = ttsh_set_launch_mode(d, t_mode[1] < t_mode[0] ? 1 : 0)) != TTSH_OK) return st;
+  return ttsh_get_plan(d, plan);
+}
+
+ttsh_status ttsh_set_launch_mode(ttsh_domain* d, int32_t pdl) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  if (pdl != 0 && pdl != 1) return fail(TTSH_E_INVALID, "launch mode must be 0 or 1");
+  if (pdl != d->dev.pdl) {
+    if (d->graph) {
+      cudaGraphExecDestroy(d->graph);
+      d->graph = nullptr;
+      d->graph_len = 0;
+    }
+    drop_record_graph(d);
+    d->dev.pdl = pdl;
+  }
+  return TTSH_OK;
 }
 
 ttsh_status ttsh_get_plan(ttsh_domain* d, int32_t* plan) {
@@ -993,7 +1065,7 @@ ttsh_status ttsh_get_plan(ttsh_domain* d, int32_t* plan) {
     plan[4] = d->ops.col_step[d->cv].pe;
     plan[5] = d->ops.n_row_variants;
     plan[6] = d->ops.n_col_variants;
-    plan[7] = 0;
+    plan[7] = d->dev.pdl;
   }
   return TTSH_OK;
 }

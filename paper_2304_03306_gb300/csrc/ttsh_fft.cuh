@@ -126,6 +126,12 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+// Programmatic dependent launch: let the next kernel in the stream start its prologue, and
+// wait until the previous kernel has completed and its writes are visible.  Both are no-ops
+// for a kernel launched without the programmatic-serialization attribute.
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 template <int BYTES>
 __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
   if constexpr (BYTES == 16) cp_async16(smem, gmem);

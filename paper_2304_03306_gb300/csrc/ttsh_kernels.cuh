@@ -131,17 +131,26 @@ struct RowGeo {
   static constexpr bool STAGE_K = KS_BYTES > 0 && TW_BYTES + BUF_BYTES + KS_BYTES + RED_BYTES <= kSmemLimit;
   static constexpr bool STAGE_G = GIN_BYTES > 0 &&
       TW_BYTES + BUF_BYTES + GIN_BYTES + (STAGE_K ? KS_BYTES : 0) + RED_BYTES <= kSmemLimit;
+  // step kernel: the forward transforms get buffers of their own when they fit, so that the
+  // real-space terms can be the first forward stage's input functor (read from the inverse
+  // buffers, no in-place pass)
+  // (float only: in double the duplicated c1 arithmetic costs more DP-pipe time than the
+  // saved pass)
+  static constexpr bool SEPARATE = KIND == ROW_STEP && sizeof(T) == 4 && STAGE_K &&
+      TW_BYTES + 2 * BUF_BYTES + (STAGE_G ? GIN_BYTES : 0) + KS_BYTES <= kSmemLimit;
   static constexpr int OFF_BUF = TW_BYTES;
   static constexpr int OFF_GIN = OFF_BUF + BUF_BYTES;
   static constexpr int OFF_KS = OFF_GIN + (STAGE_G ? GIN_BYTES : 0);
   static constexpr int OFF_RED = OFF_KS + (STAGE_K ? KS_BYTES : 0);
-  static constexpr int SMEM = OFF_RED + RED_BYTES;
+  static constexpr int OFF_FWD = OFF_RED + RED_BYTES;
+  static constexpr int SMEM = OFF_FWD + (SEPARATE ? BUF_BYTES : 0);
   static constexpr int NT = cmax(64, cmin(1024, F * R * TT));
   static constexpr int SEG = R * CB;                        // bytes per (plane, mx) segment
   static constexpr int CHUNK = SEG % 16 == 0 ? 16 : 8;
   static constexpr bool VALID = SMEM + (KIND == ROW_STEP ? kRecSmem : 0) <= 227 * 1024 && N % R == 0 &&
                                 R <= N && TT <= 1024 && NT % TT == 0;
-  static_assert(OFF_BUF % 16 == 0 && OFF_GIN % 16 == 0 && OFF_KS % 16 == 0 && OFF_RED % 16 == 0,
+  static_assert(OFF_BUF % 16 == 0 && OFF_GIN % 16 == 0 && OFF_KS % 16 == 0 && OFF_RED % 16 == 0 &&
+                OFF_FWD % 16 == 0,
                 "row pass shared-memory regions must be 16-byte aligned");
 };
 
@@ -231,6 +240,8 @@ __device__ __forceinline__ void record_partials(const Args<T>& A, int blk, int y
 // tree in warp 0) and append {step, energy, enstrophy, psi, non-finite count}.
 template <typename T>
 __device__ __forceinline__ void record_sample(const Args<T>& A) {
+  griddep_launch();
+  griddep_wait();   // the row pass's partials
   if (threadIdx.x >= 32) return;
   RecCtl* c = A.recctl;
   const int lane = threadIdx.x;
@@ -274,10 +285,18 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
   const int y0 = blk * R;
   const int tid = threadIdx.x;
 
-  // ---- stage: twiddles, the G tile (R consecutive y of every stored column), the K rows ----
+  // ---- stage: twiddles and the K rows (inputs no previous kernel writes), then, once the
+  // previous kernel has finished, the G tile (R consecutive y of every stored column) ----
   const TwTab<T, N> tw = TwTab<T, N>::fill(reinterpret_cast<cplx<T>*>(smem_raw), A.tw, tid, NT);
   cplx<T>* stab = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_STAB);
   StageTab<T, L, PE>::template fill<N>(stab, A.tw, tid, NT);
+  if constexpr (Geo::STAGE_K) {
+    constexpr int NCH = R * N * (int)sizeof(T) / 16;
+    const char* src = reinterpret_cast<const char*>(A.K + (size_t)y0 * N);
+    for (int i = tid; i < NCH; i += NT) cp_async16(reinterpret_cast<char*>(ks) + 16 * i, src + 16 * i);
+  }
+  griddep_launch();
+  griddep_wait();
   if constexpr (Geo::STAGE_G) {
     constexpr int CPS = Geo::SEG / Geo::CHUNK;   // chunks per segment
     constexpr int PLANE0 = 0;
@@ -287,11 +306,6 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
       const char* src = reinterpret_cast<const char*>(A.G + ((size_t)(PLANE0 * H + t)) * N + y0) + c * Geo::CHUNK;
       cp_async<Geo::CHUNK>(reinterpret_cast<char*>(gin + (size_t)t * R) + c * Geo::CHUNK, src);
     }
-  }
-  if constexpr (Geo::STAGE_K) {
-    constexpr int NCH = R * N * (int)sizeof(T) / 16;
-    const char* src = reinterpret_cast<const char*>(A.K + (size_t)y0 * N);
-    for (int i = tid; i < NCH; i += NT) cp_async16(reinterpret_cast<char*>(ks) + 16 * i, src + 16 * i);
   }
   cp_async_wait_all();   // tables and staged inputs
   __syncthreads();
@@ -330,7 +344,30 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
     return (x & 1) ? c.y : c.x;
   };
 
-  if constexpr (KIND == ROW_STEP) {
+  cplx<T>* fw = sm;   // buffers of the forward transforms
+  if constexpr (KIND == ROW_STEP && Geo::SEPARATE) {
+    if (A.rec != nullptr) record_partials<T, N, R, NT>(A, blk, y0, rl);
+    fw = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_FWD);
+    // F0..F2 at complex slot k of row r (real points 2k in .x, 2k + 1 in .y), computed from
+    // omega, v_x, v_y and K as the forward transforms' input; same arithmetic as the
+    // in-place loop below
+    auto rhs = [&](int bt, int k) -> cplx<T> {
+      const int f = bt / R, r = bt % R;
+      const cplx<T> wz = sm[(0 * R + r) * LP + padi<PS>(k)];
+      const T k0 = ks[r * N + 2 * k], k1 = ks[r * N + 2 * k + 1];
+      if (f == 2) return mk<T>(-(A.gw * k0) * wz.x, -(A.gw * k1) * wz.y);
+      const cplx<T> vxz = sm[(1 * R + r) * LP + padi<PS>(k)];
+      const cplx<T> vyz = sm[(2 * R + r) * LP + padi<PS>(k)];
+      auto F = [&](T w, T vx, T vy, T Kv) -> T {
+        const T v2 = fma(vx, vx, vy * vy);
+        const T c1 = fma(-A.b, v2, -(A.gv * Kv));
+        const T lw = A.lam * w;
+        return f == 0 ? fma(c1, vx, lw * vy) : fma(c1, vy, -(lw * vx));
+      };
+      return mk<T>(F(wz.x, vxz.x, vyz.x, k0), F(wz.y, vxz.y, vyz.y, k1));
+    };
+    fft_batch<T, L, PE, -1, NT, N, LP>(fw, FF * R, tw, stab, rhs);
+  } else if constexpr (KIND == ROW_STEP) {
     if (A.rec != nullptr) record_partials<T, N, R, NT>(A, blk, y0, rl);
     for (int e = tid; e < R * N; e += NT) {
       const int r = e / N, x = e % N;
@@ -397,13 +434,13 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
 
   // ---- forward row transforms (R2C), keep mx <= N/4 ----
   if constexpr (FF > 0) {
-    fft_batch<T, L, PE, -1, NT, N, LP>(sm, FF * R, tw, stab);
+    if constexpr (!Geo::SEPARATE) fft_batch<T, L, PE, -1, NT, N, LP>(sm, FF * R, tw, stab);
     for (int e = tid; e < FF * R * H; e += NT) {
       const int r = e % R;
       const int t = e / R;
       const int k = t % H;
       const int f = t / H;
-      const cplx<T>* row = sm + (f * R + r) * LP;
+      const cplx<T>* row = fw + (f * R + r) * LP;
       const cplx<T> Zk = row[padi<PS>(k)];
       const cplx<T> Zm = conjg(row[padi<PS>((L - k) & (L - 1))]);
       const cplx<T> s = Zk + Zm;
@@ -436,6 +473,8 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
   const TwTab<T, N> tw = TwTab<T, N>::fill(reinterpret_cast<cplx<T>*>(smem_raw), A.tw, tid, NT);
   cplx<T>* stab = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_STAB);
   StageTab<T, N, PE>::template fill<N>(stab, A.tw, tid, NT);
+  griddep_launch();
+  griddep_wait();   // everything below reads what the previous kernel wrote
   auto ky_of = [](int j) { return j <= M ? j : j - NK; };
   // async copy of nb contiguous columns of Rr (fields f0..f0+nb-1) into the padded buffers
   auto stage_columns = [&](int f0, int nb) {

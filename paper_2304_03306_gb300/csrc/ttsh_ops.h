@@ -25,6 +25,7 @@ struct DomainDev {
   double a, b, lam, gv, gw, dx, dt;
   double cx, cy;   // centre for the order parameter
   int n;
+  int pdl;         // launch the step kernels with programmatic dependent launch
 };
 
 enum { K_ROW_STEP = 0, K_ROW_FWD_VEL = 1, K_ROW_FWD_MASK = 2, K_ROW_INV_FIELDS = 3,

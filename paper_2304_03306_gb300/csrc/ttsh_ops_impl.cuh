@@ -47,14 +47,37 @@ static cudaError_t set_smem(K kernel, int bytes, std::atomic<int>& done) {
   return e;
 }
 
+// Launch, optionally as a programmatic dependent launch: the kernel may start while the
+// previous kernel in the stream is still running; it waits (griddepcontrol.wait) before it
+// touches anything that kernel writes.
+template <typename T>
+static cudaError_t launch_k(void (*kernel)(Args<T>), int grid, int block, int smem, cudaStream_t s, bool pdl,
+                            const Args<T>& a) {
+  if (!pdl) {
+    kernel<<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 template <typename T, int N, int KIND, int R = default_rows<T, N>(), int PE = default_row_pe<T, N>()>
 static cudaError_t launch_row_kind(const DomainDev& d, cudaStream_t s) {
   using Geo = RowGeo<T, N, KIND, R, PE>;
   static std::atomic<int> done{0};
   cudaError_t e = set_smem(row_kernel<T, N, KIND, R, PE>, Geo::SMEM, done);
   if (e != cudaSuccess) return e;
-  row_kernel<T, N, KIND, R, PE><<<N / R, Geo::NT, Geo::SMEM, s>>>(make_args<T>(d));
-  return cudaGetLastError();
+  return launch_k<T>(row_kernel<T, N, KIND, R, PE>, N / R, Geo::NT, Geo::SMEM, s, KIND == ROW_STEP && d.pdl,
+                     make_args<T>(d));
 }
 
 template <typename T, int N, int MODE, int PE = default_col_pe<T, N>()>
@@ -65,8 +88,8 @@ static cudaError_t launch_col_mode(const DomainDev& d, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   // a recorded step adds one block that finishes the time-series sample
   const int extra = (MODE == COL_STEP && d.rec != nullptr) ? 1 : 0;
-  col_kernel<T, N, MODE, PE><<<Geo::H + extra, Geo::NT, Geo::SMEM, s>>>(make_args<T>(d));
-  return cudaGetLastError();
+  return launch_k<T>(col_kernel<T, N, MODE, PE>, Geo::H + extra, Geo::NT, Geo::SMEM, s, MODE == COL_STEP && d.pdl,
+                     make_args<T>(d));
 }
 
 template <typename T, int N>

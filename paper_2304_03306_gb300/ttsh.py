@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH):
         "ttsh_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
         "ttsh_get_plan": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
         "ttsh_set_plan": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+        "ttsh_set_launch_mode": (ctypes.c_int, [_P, ctypes.c_int32]),
         "ttsh_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, _P, ctypes.POINTER(_P)]),
         "ttsh_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
         "ttsh_batch_synchronize": (ctypes.c_int, [_P]),
@@ -236,7 +237,7 @@ def ttsh_time_kernels(h, iters: int):
 
 
 _PLAN_KEYS = ("row_variant", "col_variant", "rows_per_block", "row_points_per_thread",
-              "col_points_per_thread", "n_row_variants", "n_col_variants")
+              "col_points_per_thread", "n_row_variants", "n_col_variants", "pdl")
 
 
 def _plan_dict(buf):
@@ -257,6 +258,10 @@ def ttsh_get_plan(h) -> dict:
 
 def ttsh_set_plan(h, row_variant: int, col_variant: int):
     _check(load_library().ttsh_set_plan(h, int(row_variant), int(col_variant)))
+
+
+def ttsh_set_launch_mode(h, pdl: int):
+    _check(load_library().ttsh_set_launch_mode(h, int(pdl)))
 
 
 def ttsh_batch_create(handles, stream: int | None = None):
@@ -489,8 +494,10 @@ class Domain:
     def plan(self) -> dict:
         return ttsh_get_plan(self.h)
 
-    def set_plan(self, row_variant: int, col_variant: int):
+    def set_plan(self, row_variant: int, col_variant: int, pdl: int | None = None):
         ttsh_set_plan(self.h, row_variant, col_variant)
+        if pdl is not None:
+            ttsh_set_launch_mode(self.h, pdl)
 
     def time_kernels(self, iters: int):
         """Mean (row pass, column pass) launch durations in ms, state restored afterwards."""

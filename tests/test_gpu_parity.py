@@ -261,6 +261,27 @@ def test_graph_replay_equals_eager_launches(T):
     assert np.array_equal(a.spectral_state()[0], b.spectral_state()[0])
 
 
+@pytest.mark.parametrize("prec", [32, 64])
+def test_launch_modes_are_bit_identical(T, prec):
+    n, dx = 64, 0.25
+    mask = ti.circle_mask(n, dx, 5.2)
+    vx, vy = ti.noise_velocity(mask, 12, 0.3)
+    a = T.Domain(mask, n, dx, precision=prec)
+    b = T.Domain(mask, n, dx, precision=prec)
+    for d in (a, b):
+        d.set_velocity(vx, vy)
+    b.set_plan(0, 0, pdl=1)
+    assert b.plan()["pdl"] == 1 and a.plan()["pdl"] == 0
+    a.step(300)          # graph replays plus eager steps
+    b.step(300)
+    assert np.array_equal(a.spectral_state()[0], b.spectral_state()[0])
+    sa, sb = a.record(130, 10), b.record(130, 10)
+    assert np.array_equal(sa, sb)
+    assert np.array_equal(a.spectral_state()[0], b.spectral_state()[0])
+    with pytest.raises(T.TTSHError):
+        T.ttsh_set_launch_mode(a.h, 2)
+
+
 def test_fp64_8192_is_unsupported(T):
     with pytest.raises(T.TTSHError) as e:
         T.Domain(np.zeros((8192, 8192), np.uint8), 8192, 0.005, precision=64)
