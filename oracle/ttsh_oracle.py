@@ -312,3 +312,79 @@ def dumbbell_order_parameter(omega, p: Params, centres, radius):
         peaks.append(float(omega.reshape(-1)[int(np.argmax(flat))]))
     a, b = peaks
     return abs(a + b) / (abs(a) + abs(b)), a, b
+
+
+# ----------------------------------------------------------------------------------------
+# Lyapunov exponents (Sec. III.C, "Lyapunov analysis"): independent perturbations evolved
+# along with the solution, growth rates from QR decompositions (the standard method the
+# paper cites: Shimada & Nagashima 1979, Benettin et al. 1980)
+# ----------------------------------------------------------------------------------------
+
+def state_vector(s: State, p: Params) -> np.ndarray:
+    """The state as a real vector: (Re, Im) of omega^ on the stored half spectrum (columns
+    mx = 0..N/4, entries my = 0..N/4 then -N/4..-1, interleaved re/im), then v^(0)."""
+    n, M = p.n, p.n // 4
+    ky = np.concatenate([np.arange(0, M + 1), np.arange(-M, 0)])
+    half = s.w_hat[np.ix_(ky % n, np.arange(M + 1))].T          # [mx][j]
+    v0 = (np.real(dft2(s.vx)[0, 0]), np.real(dft2(s.vy)[0, 0]))
+    return np.concatenate([np.stack([half.real, half.imag], axis=-1).reshape(-1), np.array(v0)])
+
+
+def vector_state(u: np.ndarray, p: Params) -> State:
+    """Inverse of state_vector: the mx < 0 half of omega^ follows from omega^(-m) = conj
+    omega^(m); the velocity is the stream-function velocity plus v^(0)."""
+    n, M = p.n, p.n // 4
+    NK = 2 * M + 1
+    half = u[:-2].reshape(M + 1, NK, 2)
+    half = half[..., 0] + 1j * half[..., 1]
+    ky = np.concatenate([np.arange(0, M + 1), np.arange(-M, 0)])
+    w_hat = np.zeros((n, n), dtype=complex)
+    for mx in range(M + 1):
+        w_hat[ky % n, mx] = half[mx]
+        if mx > 0:
+            w_hat[(-ky) % n, (-mx) % n] = np.conj(half[mx])
+    return from_spectral(w_hat, (u[-2], u[-1]), p)
+
+
+def state_weights(p: Params) -> np.ndarray:
+    """Weights that make sum_i w_i u_i u'_i the real-space inner product sum_x (omega omega')
+    plus v^(0).v'^(0) (Parseval): 1 on the mx = 0 column, 2 on mx > 0 columns (they stand for
+    +-mx), 1 on the mean flow."""
+    M = p.n // 4
+    NK = 2 * M + 1
+    w = np.ones((M + 1, NK, 2))
+    w[1:] = 2.0
+    return np.concatenate([w.reshape(-1), np.ones(2)])
+
+
+def lyapunov(s: State, K: np.ndarray, p: Params, q0: np.ndarray, eps: float, nsteps: int,
+             interval: int):
+    """Lyapunov exponents of the trajectory starting at s.  q0: (k, D) initial perturbation
+    directions (state_vector layout).  Every `interval` steps each perturbation, evolved as
+    the finite difference (step^interval(s + eps q) - step^interval(s)) / eps of the scheme
+    of Algorithm 1, is re-orthonormalised by a QR decomposition (weighted inner product of
+    state_weights, R with a positive diagonal); the exponents are the accumulated log R_ii
+    divided by the elapsed time.  Returns (exponents, rates of the last interval, final base
+    state, final orthonormal directions)."""
+    if nsteps % interval:
+        raise ValueError("nsteps must be a multiple of interval")
+    sw = np.sqrt(state_weights(p))
+
+    def orthonormal(A):                       # columns of A (D, k) -> Q (D, k), diag(R)
+        Qw, R = np.linalg.qr(sw[:, None] * A)
+        sg = np.sign(np.diag(R))
+        return (Qw * sg) / sw[:, None], np.abs(np.diag(R))
+
+    Q, _ = orthonormal(np.asarray(q0, dtype=np.float64).T)
+    logs = np.zeros(Q.shape[1])
+    last = np.zeros(Q.shape[1])
+    for _ in range(nsteps // interval):
+        u0 = state_vector(s, p)
+        perts = [vector_state(u0 + eps * Q[:, i], p) for i in range(Q.shape[1])]
+        s = run(s, K, p, interval)
+        u1 = state_vector(s, p)
+        D = np.stack([(state_vector(run(pi, K, p, interval), p) - u1) / eps for pi in perts], axis=1)
+        Q, r = orthonormal(D)
+        logs += np.log(r)
+        last = np.log(r) / (interval * p.dt)
+    return logs / (nsteps * p.dt), last, s, Q.T

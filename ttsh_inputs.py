@@ -102,6 +102,28 @@ def noise_velocity(mask: np.ndarray, seed: int, amplitude: float = 0.01):
 
 # Synthetic workloads with the paper's shapes.  Box lengths and radii follow the paper's
 # regimes (single vortex near R = 5.2, oscillating pair near R = 5.4, turbulence for R >= 8).
+def perturbation_directions(n: int, k: int, seed: int) -> np.ndarray:
+    """k seeded random perturbation directions of a state, as (k, D) doubles in the stored
+    half-spectrum layout (columns mx = 0..n/4, entries my = 0..n/4 then -n/4..-1, interleaved
+    re/im) followed by the two mean-flow components: uniform in [-1, 1) on the modes
+    0 < mx^2 + my^2 <= (n/4)^2, zero elsewhere, the mx = 0 column Hermitian (the my < 0
+    entries are the conjugates of the my > 0 ones, my = 0 is real) like a state's."""
+    M = n // 4
+    NK = 2 * M + 1
+    D = 2 * (M + 1) * NK + 2
+    u = 2.0 * uniform01(seed, np.arange(k * D, dtype=np.uint64)).reshape(k, D) - 1.0
+    spec = u[:, :-2].reshape(k, M + 1, NK, 2)
+    my = np.array([j if j <= M else j - NK for j in range(NK)])
+    mx = np.arange(M + 1)
+    m2 = mx[:, None] ** 2 + my[None, :] ** 2
+    spec[:, (m2 == 0) | (m2 > M * M), :] = 0.0
+    spec[:, 0, 0, 1] = 0.0
+    for j in range(1, M + 1):
+        spec[:, 0, NK - j, 0] = spec[:, 0, j, 0]
+        spec[:, 0, NK - j, 1] = -spec[:, 0, j, 1]
+    return np.concatenate([spec.reshape(k, -1), u[:, -2:]], axis=1)
+
+
 WORKLOADS = {
     "circle64_fp64": dict(n=64, dx=0.25, radius=5.2, seed=1, steps=2000),
     "circle512": dict(n=512, dx=0.04, radius=5.4, seed=2, steps=20000),
