@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-lyap", action="store_true")
     return ap.parse_args()
 
 
@@ -347,7 +348,7 @@ def run_ours(args, rank, world, local_rank):
         bt.step(Sb)
         bt.synchronize()
         barrier()
-        tb = max_over_ranks(timed_segments(bt, K, Sb))
+        tb = max_over_ranks(timed_segments(bt, K, Sb, record=False))
         pts = sum(dspec["n"] ** 2 for dspec in sweep)
         batched = {"value": world * pts * Sb * K / tb, "unit": UNIT, "domains": len(sweep),
                    "grid_points": pts, "solver_steps_per_step": Sb, "launch_groups": bt.groups,
@@ -357,6 +358,35 @@ def run_ours(args, rank, world, local_rank):
         bt.close()
         for o in objs:
             o.close()
+
+    # ---- Lyapunov analysis: the workload's domain with 8 perturbed copies ----
+    lyap = None
+    if not args.no_lyap and rank == 0:
+        kl, il = 8, 10
+        dl = ttsh.Domain(mask, n, dx, precision=32, stream=stream.cuda_stream)
+        dl.set_velocity(vx0, vy0)
+        dl.set_plan(plan32["row_variant"], plan32["col_variant"], plan32["pdl"])
+        dl.step(200)
+        w0, m0 = dl.spectral_state()
+        u0 = np.concatenate([np.stack([w0.real, w0.imag], axis=-1).reshape(-1), m0])
+        L = ttsh.Lyapunov(dl, ti.perturbation_directions(n, kl, 11), 1e-3 * np.linalg.norm(u0))
+        L.step(10 * il, il)   # warm-up (graphs, attributes)
+        dl.synchronize()
+        Sl = max(il, (S // 40) // il * il)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.step(Sl, il)
+        e1.record(stream)
+        stream.synchronize()
+        tl = e0.elapsed_time(e1) / 1e3
+        ex, last = L.result()
+        lyap = {"perturbations": kl, "interval": il, "solver_steps": Sl,
+                "ms_per_solver_step": 1e3 * tl / Sl,
+                "grid_point_steps_per_s": (kl + 1) * n * n * Sl / tl,
+                "exponents": [float(x) for x in ex],
+                "note": "FP32 domain, eps = 1e-3 of the state norm; exponents over a short run (not converged)"}
+        L.close()
+        dl.close()
 
     # ---- learned corrector: train on solver-generated data, evaluate on a held-out radius ----
     surrogate = None
@@ -470,7 +500,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e, "gpu_launches": K * (2 * S + (cap + 1 if RE > 0 else 0)), "clocks": clk, "roofline": roofline,
         "value_without_time_series": world * n * n * S * K / t_plain,
         "time_series_last_sample": series_last,
-        "cpu_baseline": cpu, "fp64": fp64, "batched": batched, "surrogate": surrogate,
+        "cpu_baseline": cpu, "fp64": fp64, "batched": batched, "surrogate": surrogate, "lyapunov": lyap,
         "diagnostics_after": {"energy": diag["energy"], "psi": diag["psi"], "nonfinite": diag["nonfinite"]},
         "ms_per_solver_step": 1e3 * t32 / (K * S),
     }

@@ -224,6 +224,38 @@ ttsh_status ttsh_set_launch_mode(ttsh_domain* d, int32_t pdl);
 ttsh_status ttsh_step_noalloc(const ttsh_params* p, const void* K, void* w_hat, void* v0,
                               int64_t nsteps, void* stream);
 
+/* Lyapunov exponents of a domain's trajectory (Sec. III.C: growth rates of independent
+ * perturbations delta omega_i evolved along with omega, obtained from QR decompositions as in
+ * Shimada & Nagashima 1979 and Benettin et al. 1980).  The paper does not say how the
+ * perturbations are evolved; here each is a copy of the domain started at base + eps q_i and
+ * stepped with it (batched with it for n <= 1024), so a perturbation evolves as the finite
+ * difference (copy - base) / eps of the scheme of Algorithm 1.  After every `interval` steps
+ * the k differences are re-orthonormalised by classical Gram-Schmidt applied twice, in
+ * double precision, log R_ii is accumulated and the copies are reset to base + eps q_i.
+ * State vectors (D = 2 H NK + 2 doubles, H = N/4 + 1, NK = N/2 + 1) are omega^ in the stored
+ * half-spectrum layout (interleaved re/im, as ttsh_get_spectral_state) followed by v^(0); the
+ * inner product weights the mx > 0 columns by 2 (they stand for +-mx), which makes it the
+ * real-space sum_x omega omega' plus v^(0).v'^(0).
+ *   create   base: the domain whose trajectory is analysed (it is stepped by ttsh_lyap_step);
+ *            k in [1, 16] perturbations; eps > 0 their size in that norm; q0: host, k x D
+ *            doubles, the initial directions (orthonormalised on the device; they should be
+ *            Hermitian in the mx = 0 column and zero outside the 1/2-rule disc, as a state is).
+ *            The copies use k extra domain workspaces.  Synchronises.
+ *   step     advance base and copies by nsteps (a multiple of interval; interval fixed for
+ *            the run) with a renormalisation after every interval.  Asynchronous.
+ *   result   exponents[k] = accumulated log R_ii / elapsed time, largest first in the limit;
+ *            last_rates[k] (may be NULL) = log R_ii / (interval dt) of the last interval.
+ *            TTSH_E_INVALID before the first interval.  Synchronises.
+ *   directions  the current orthonormal directions q_i (host, k x D doubles).  Synchronises.
+ * Not in the paper's interface: these entry points are this library's form of its Lyapunov
+ * analysis. */
+typedef struct ttsh_lyap ttsh_lyap;
+ttsh_status ttsh_lyap_create(ttsh_domain* base, int32_t k, double eps, const double* q0, ttsh_lyap** out);
+ttsh_status ttsh_lyap_step(ttsh_lyap* L, int64_t nsteps, int32_t interval);
+ttsh_status ttsh_lyap_result(ttsh_lyap* L, double* exponents, double* last_rates);
+ttsh_status ttsh_lyap_directions(ttsh_lyap* L, double* q);
+void ttsh_lyap_destroy(ttsh_lyap* L);
+
 /* Batched stepping of many independent domains, as the paper's radius and dumbbell sweeps
  * (Sec. III.C, Sec. IV) need: dozens of small domains of uneven sizes advanced together.
  * ttsh_batch_create groups the domains by (precision, n, plan); every group advances in one

@@ -374,6 +374,70 @@ int domain_add_vorticity_from_staging(ttsh_domain* d) {
   if (st != TTSH_OK) return st;
   return run_col(d, K_COL_ADDW, d->stream);
 }
+double domain_dt(const ttsh_domain* d) { return d->p.dt; }
+int domain_refresh(ttsh_domain* d) { return run_col(d, K_COL_PROLOGUE, d->stream); }
+
+// A second domain with the same parameters, processed mask, twiddles, plan, launch mode,
+// stream and state as src (device-to-device copies; the library allocates its workspace).
+int domain_clone(const ttsh_domain* src, ttsh_domain** out) {
+  *out = nullptr;
+  ttsh_domain* d = new ttsh_domain();
+  d->p = src->p;
+  d->n = src->n;
+  d->M = src->M;
+  d->H = src->H;
+  d->NK = src->NK;
+  d->elt = src->elt;
+  d->stream = src->stream;
+  d->capture = nullptr;
+  d->ops = src->ops;
+  d->steps = src->steps;
+  d->graph = nullptr;
+  d->graph_len = 0;
+  d->rv = src->rv;
+  d->cv = src->cv;
+  d->lay = src->lay;
+  d->owns_ws = true;
+  d->ws = nullptr;
+  auto cleanup = [&](ttsh_status s) {
+    ttsh_destroy_domain(d);
+    return (int)s;
+  };
+  cudaError_t e = cudaMalloc(&d->ws, d->lay.total);
+  if (e != cudaSuccess) {
+    d->ws = nullptr;
+    return cleanup(cuda_fail(e, "workspace allocation"));
+  }
+  e = cudaStreamCreateWithFlags(&d->capture, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "capture stream"));
+  d->dev = src->dev;   // constants, centre, launch mode; pointers rebased below
+  char* base = static_cast<char*>(d->ws);
+  DomainDev& v = d->dev;
+  v.what = base + d->lay.what;
+  v.vmean = base + d->lay.vmean;
+  v.K = base + d->lay.K;
+  v.G = base + d->lay.G;
+  v.Rr = base + d->lay.Rr;
+  v.tw = base + d->lay.tw;
+  v.real = reinterpret_cast<double*>(base + d->lay.real);
+  v.part = reinterpret_cast<double*>(base + d->lay.part);
+  v.colhist = reinterpret_cast<double*>(base + d->lay.colhist);
+  v.bad = reinterpret_cast<int*>(base + d->lay.bad);
+  v.out = reinterpret_cast<double*>(base + d->lay.out);
+  v.rec = nullptr;
+  v.recctl = nullptr;
+  const size_t NN = (size_t)d->n * d->n;
+  const size_t wbytes = (size_t)d->H * d->NK * 2 * d->elt;
+  e = cudaMemcpyAsync(v.K, src->dev.K, NN * d->elt, cudaMemcpyDeviceToDevice, d->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v.tw, src->dev.tw, (size_t)d->n * 2 * d->elt, cudaMemcpyDeviceToDevice, d->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v.what, src->dev.what, wbytes, cudaMemcpyDeviceToDevice, d->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v.vmean, src->dev.vmean, 64, cudaMemcpyDeviceToDevice, d->stream);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "clone copies"));
+  ttsh_status st = run_col(d, K_COL_PROLOGUE, d->stream);
+  if (st != TTSH_OK) return cleanup(st);
+  *out = d;
+  return TTSH_OK;
+}
 
 // Spectral restriction of a fine state onto a coarse grid of the same box: the coarse
 // unitary coefficients are the fine ones times Nc/Nf on the coarse 1/2-rule disc.

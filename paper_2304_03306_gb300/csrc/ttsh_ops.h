@@ -96,6 +96,11 @@ int domain_fields_to_staging(ttsh_domain* d);
 int domain_add_vorticity_from_staging(ttsh_domain* d);
 // Adjust the step counter (for steps replayed from a graph the domain did not record).
 void domain_add_steps(ttsh_domain* d, int64_t n);
+double domain_dt(const ttsh_domain* d);
+// Rebuild the inter-pass buffers from the spectral state (after writing it on the device).
+int domain_refresh(ttsh_domain* d);
+// Copy of a domain (parameters, mask, plan, stream, state) in a new library-owned workspace.
+int domain_clone(const ttsh_domain* src, ttsh_domain** out);
 
 cudaError_t launch_diag_reduce(const double* part, int nblocks, double* out, cudaStream_t s);
 cudaError_t launch_spectrum_reduce(const double* colhist, int ncols, int nbins, double scale,

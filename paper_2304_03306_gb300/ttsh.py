@@ -106,6 +106,11 @@ def load_library(path: str = LIB_PATH):
         "ttsh_fno_residual": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32]),
         "ttsh_fno_correct": (ctypes.c_int, [_P, _P, _P]),
         "ttsh_fno_rollout": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int32, _P]),
+        "ttsh_lyap_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, _D, ctypes.POINTER(_P)]),
+        "ttsh_lyap_step": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32]),
+        "ttsh_lyap_result": (ctypes.c_int, [_P, _D, _D]),
+        "ttsh_lyap_directions": (ctypes.c_int, [_P, _D]),
+        "ttsh_lyap_destroy": (None, [_P]),
         "ttsh_step_count": (ctypes.c_int64, [_P]),
         "ttsh_step_noalloc": (ctypes.c_int, [ctypes.POINTER(ttsh_params), _P, _P, _P, ctypes.c_int64, _P]),
         "ttsh_last_error": (ctypes.c_char_p, []),
@@ -520,3 +525,38 @@ class Domain:
     def dumbbell_order(self, centres, radius: float):
         """(Psi_2, omega at the left peak, omega at the right peak)."""
         return ttsh_dumbbell_order(self.h, centres, radius)
+
+
+class Lyapunov:
+    """Lyapunov exponents of a Domain's trajectory (ttsh_lyap_*): k perturbed copies stepped
+    with it, re-orthonormalised every `interval` steps."""
+
+    def __init__(self, dom: "Domain", q0, eps: float):
+        q0 = np.ascontiguousarray(q0, dtype=np.float64)
+        self.k, self.D = q0.shape
+        self.h = _P()
+        _check(load_library().ttsh_lyap_create(dom.h, self.k, float(eps), _dptr(q0), ctypes.byref(self.h)))
+
+    def step(self, nsteps: int, interval: int):
+        _check(load_library().ttsh_lyap_step(self.h, int(nsteps), int(interval)))
+
+    def result(self):
+        ex, last = np.empty(self.k), np.empty(self.k)
+        _check(load_library().ttsh_lyap_result(self.h, _dptr(ex), _dptr(last)))
+        return ex, last
+
+    def directions(self):
+        q = np.empty((self.k, self.D))
+        _check(load_library().ttsh_lyap_directions(self.h, _dptr(q)))
+        return q
+
+    def close(self):
+        if self.h:
+            load_library().ttsh_lyap_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
