@@ -142,10 +142,10 @@ def profile_record(fname, key, kernel, n, precision, plan):
     """A per-launch counter from a committed ncu summary, if it was taken on the current
     kernel sources and on the tile variant the autotuner chose."""
     try:
-        t = json.load(open(os.path.join(ROOT, "profiles", fname)))
-        e = t[f"{kernel}:{n}:{precision}"]
-        if e.get("csrc_hash") == csrc_hash() and list(e["variant"]) == plan_variant(kernel, plan):
-            return float(e[key])
+        t = json.load(open(os.path.join(ROOT, "profiles", fname)))["records"]
+        for e in t[f"{kernel}:{n}:{precision}"]:
+            if e.get("csrc_hash") == csrc_hash() and list(e["variant"]) == plan_variant(kernel, plan):
+                return float(e[key])
     except Exception:
         pass
     return None
