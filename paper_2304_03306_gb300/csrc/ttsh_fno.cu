@@ -119,14 +119,6 @@ cudaError_t sgemm(bool ta, bool tb, int M, int N, int K, int batch, float alpha,
 // ---------------------------------------------------------------------------------------
 constexpr int CW = 32;   // width the tensor-core kernels are written for
 
-__device__ __forceinline__ void mma16816(float* d, const unsigned* a, const unsigned* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
   return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
@@ -143,63 +135,137 @@ struct PwArgs {
   float* h;                 // P x 32: GELU(z) (forward)
   __nv_bfloat16* hb;        // P x 32: GELU(z) in BF16 (forward)
   long long P;
+  int* err;                 // set to 1 if a tensor-core completion wait ran out
 };
 
-// One warp computes 16 rows x 32 columns (4 n-tiles x 2 k-steps of m16n8k16).
+// ---------------------------------------------------------------------------------------
+// Channel mixing on the 5th-generation tensor cores (tcgen05).  A CTA of 4 warps owns a
+// 128 x 32 FP32 accumulator in tensor memory; per 128-row tile it stages A (128 x 32 BF16)
+// in shared memory in the canonical K-major layout without swizzle (8-row x 16-byte core
+// matrices, K-adjacent core matrices 128 B apart, row groups 512 B apart), one thread issues
+// two tcgen05.mma (M = 128, N = 32, K = 16 each; B = the 32 x 32 weight, staged once), the
+// completion is signalled on an mbarrier by tcgen05.commit, and each warp reads its 32
+// accumulator lanes with tcgen05.ld for the fused bias / residual / GELU epilogue.  Every
+// wait is bounded: on time-out the CTA records the error, releases its tensor memory and
+// returns.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride (M/N) byte offsets,
+// descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+constexpr int kTcRows = 128;
+constexpr long long kTcSpin = 1ll << 24;   // bound on the completion wait (polls)
+
+// (r, k) of a 128 x 32 (or 32 x 32) BF16 K-major tile -> byte offset in the core-matrix layout
+__device__ __forceinline__ int core_off(int r, int kc) { return (r >> 3) * 512 + kc * 128 + (r & 7) * 16; }
+
 template <int EPI>
-__global__ void __launch_bounds__(256) pointwise_mma_kernel(PwArgs a) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const long long row0 = ((long long)blockIdx.x * 8 + warp) * 16;
-  if (row0 >= a.P) return;
-  const unsigned* A32 = reinterpret_cast<const unsigned*>(a.A);
-  const unsigned* B32 = reinterpret_cast<const unsigned*>(a.Bt);
-  unsigned af[2][4];
-#pragma unroll
-  for (int ks = 0; ks < 2; ++ks) {
-    const long long r0 = (row0 + g) * CW + ks * 16 + 2 * t, r1 = (row0 + g + 8) * CW + ks * 16 + 2 * t;
-    af[ks][0] = A32[r0 >> 1];
-    af[ks][1] = A32[r1 >> 1];
-    af[ks][2] = A32[(r0 + 8) >> 1];
-    af[ks][3] = A32[(r1 + 8) >> 1];
+__global__ void __launch_bounds__(128) pointwise_tc_kernel(PwArgs a) {
+  __shared__ __align__(1024) uint8_t sa[kTcRows * CW * 2];
+  __shared__ __align__(1024) uint8_t sb[CW * CW * 2];
+  __shared__ float sbias[CW];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int c = tid; c < CW * 4; c += 128) {
+    const int r = c >> 2, kc = c & 3;
+    *reinterpret_cast<uint4*>(sb + core_off(r, kc)) = *reinterpret_cast<const uint4*>(a.Bt + r * CW + kc * 8);
   }
-  float d[4][4];
-#pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) d[nt][q] = 0.f;
-#pragma unroll
-    for (int ks = 0; ks < 2; ++ks) {
-      const int b0 = (nt * 8 + g) * CW + ks * 16 + 2 * t;
-      unsigned bf[2] = {B32[b0 >> 1], B32[(b0 + 8) >> 1]};
-      mma16816(d[nt], af[ks], bf);
+  if (tid < CW) sbias[tid] = (EPI != EPI_BWD) ? a.bias[tid] : 0.f;
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const long long ntiles = (a.P + kTcRows - 1) / kTcRows;
+  uint32_t phase = 0;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long row0 = t * kTcRows;
+    for (int c = tid; c < kTcRows * 4; c += 128) {
+      const int r = c >> 2, kc = c & 3;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (row0 + r < a.P) v = *reinterpret_cast<const uint4*>(a.A + (row0 + r) * CW + kc * 8);
+      *reinterpret_cast<uint4*>(sa + core_off(r, kc)) = v;
     }
-  }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      constexpr uint32_t id = umma_idesc_bf16(kTcRows, CW);
 #pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const long long p = row0 + g + 8 * half;
-      const int o = nt * 8 + 2 * t;
-      const long long idx = p * CW + o;
-      float v0 = d[nt][2 * half], v1 = d[nt][2 * half + 1];
-      const float2 ad = *reinterpret_cast<const float2*>(a.add + idx);
-      v0 += ad.x;
-      v1 += ad.y;
-      if (EPI != EPI_BWD) {
-        v0 += a.bias[o];
-        v1 += a.bias[o + 1];
+      for (int ks = 0; ks < 2; ++ks) {
+        const uint64_t ad = umma_desc(smem_u32(sa) + ks * 256, 128, 512);
+        const uint64_t bd = umma_desc(smem_u32(sb) + ks * 256, 128, 512);
+        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                     ::"r"(tmem), "l"(ad), "l"(bd), "r"(id), "r"(ks) : "memory");
       }
-      *reinterpret_cast<float2*>(a.out + idx) = make_float2(v0, v1);
-      if (EPI == EPI_FWD) {
-        const float h0 = gelu(v0), h1 = gelu(v1);
-        *reinterpret_cast<float2*>(a.h + idx) = make_float2(h0, h1);
-        *reinterpret_cast<__nv_bfloat162*>(a.hb + idx) = __floats2bfloat162_rn(h0, h1);
-      } else if (EPI == EPI_FWD_LAST) {
-        *reinterpret_cast<float2*>(a.h + idx) = make_float2(v0, v1);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(&mbar)) : "memory");
+    }
+    uint32_t done = 0;
+    for (long long it = 0; it < kTcSpin && !done; ++it)
+      asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                   : "=r"(done) : "r"(smem_u32(&mbar)), "r"(phase) : "memory");
+    if (__syncthreads_or(!done)) {
+      if (tid == 0) atomicExch(a.err, 1);
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint32_t r[CW];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const long long p = row0 + warp * 32 + lane;
+    if (p < a.P) {
+#pragma unroll
+      for (int o = 0; o < CW; o += 4) {
+        const long long idx = p * CW + o;
+        const float4 ad = *reinterpret_cast<const float4*>(a.add + idx);
+        float v[4] = {__uint_as_float(r[o]) + ad.x, __uint_as_float(r[o + 1]) + ad.y,
+                      __uint_as_float(r[o + 2]) + ad.z, __uint_as_float(r[o + 3]) + ad.w};
+        if (EPI != EPI_BWD)
+          for (int q = 0; q < 4; ++q) v[q] += sbias[o + q];
+        *reinterpret_cast<float4*>(a.out + idx) = make_float4(v[0], v[1], v[2], v[3]);
+        if (EPI == EPI_FWD) {
+          const float h0 = gelu(v[0]), h1 = gelu(v[1]), h2 = gelu(v[2]), h3 = gelu(v[3]);
+          *reinterpret_cast<float4*>(a.h + idx) = make_float4(h0, h1, h2, h3);
+          *reinterpret_cast<__nv_bfloat162*>(a.hb + idx) = __floats2bfloat162_rn(h0, h1);
+          *reinterpret_cast<__nv_bfloat162*>(a.hb + idx + 2) = __floats2bfloat162_rn(h2, h3);
+        } else if (EPI == EPI_FWD_LAST) {
+          *reinterpret_cast<float4*>(a.h + idx) = make_float4(v[0], v[1], v[2], v[3]);
+        }
       }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");   // accumulator read before reuse
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
 // ---------------------------------------------------------------------------------------
@@ -645,6 +711,7 @@ struct ttsh_fno {
   __nv_bfloat16* dzb = nullptr;
   float *wpart = nullptr;
   double* lpart = nullptr;
+  int* tc_err = nullptr;        // set by the tensor-core kernels when a completion wait ran out
   int wchunk, nwblk;
   float in_scale[4] = {1, 1, 1, 1}, out_scale = 1;
   bool fused_columns = false;   // row_dft / column kernels fit in shared memory
@@ -669,6 +736,23 @@ ttsh_status fno_cuda(cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                        \
     if (e_ != cudaSuccess) return fno_cuda(e_, what); \
   } while (0)
+
+// Grid of the tensor-core kernels: one CTA per 128-row tile, at most 4 resident per SM.
+unsigned tc_grid(long long P) {
+  const long long tiles = (P + kTcRows - 1) / kTcRows;
+  return (unsigned)(tiles < 152 * 4 ? tiles : 152 * 4);
+}
+
+// Report (once) a tensor-core completion wait that ran out; called at synchronising entries.
+ttsh_status check_tc(ttsh_fno* f) {
+  int h = 0;
+  FNO_CUDA(cudaMemcpy(&h, f->tc_err, sizeof(int), cudaMemcpyDeviceToHost), "read tensor-core status");
+  if (h) {
+    cudaMemset(f->tc_err, 0, sizeof(int));
+    return fno_fail(TTSH_E_TIMEOUT, "a tensor-core completion wait ran out");
+  }
+  return TTSH_OK;
+}
 
 template <typename P>
 cudaError_t dalloc(ttsh_fno* f, P** ptr, size_t bytes) {
@@ -761,9 +845,10 @@ ttsh_status forward_impl(ttsh_fno* f, const float* x, int B, float* out, const f
     a.h = f->h[l + 1];
     a.hb = l + 1 < L ? f->hb[l + 1] : nullptr;
     a.P = P;
-    const unsigned nblk = (unsigned)((P / 16 + 7) / 8);
-    if (l + 1 < L) pointwise_mma_kernel<EPI_FWD><<<nblk, 256, 0, s>>>(a);
-    else pointwise_mma_kernel<EPI_FWD_LAST><<<nblk, 256, 0, s>>>(a);
+    a.err = f->tc_err;
+    const unsigned nblk = tc_grid(P);
+    if (l + 1 < L) pointwise_tc_kernel<EPI_FWD><<<nblk, 128, 0, s>>>(a);
+    else pointwise_tc_kernel<EPI_FWD_LAST><<<nblk, 128, 0, s>>>(a);
     FNO_CUDA(cudaGetLastError(), "pointwise layer");
   }
   const unsigned pblk = (unsigned)((P + 255) / 256);
@@ -840,7 +925,8 @@ ttsh_status backward_impl(ttsh_fno* f, const float* x, int B, const float* out) 
     a.h = nullptr;
     a.hb = nullptr;
     a.P = P;
-    pointwise_mma_kernel<EPI_BWD><<<(unsigned)((P / 16 + 7) / 8), 256, 0, s>>>(a);
+    a.err = f->tc_err;
+    pointwise_tc_kernel<EPI_BWD><<<tc_grid(P), 128, 0, s>>>(a);
     FNO_CUDA(cudaGetLastError(), "pointwise adjoint");
   }
   // lift: dWp = x^T dh0, dbp = sum dh0
@@ -939,6 +1025,8 @@ ttsh_status ttsh_fno_create(const ttsh_fno_config* cfg, uint64_t seed, void* str
   A(&f->yo, P * 4);
   A(&f->wpart, (long long)f->nwblk * (C * C + C) * 4);
   A(&f->lpart, ((P + 255) / 256) * 8);
+  A(&f->tc_err, 64);
+  if (e == cudaSuccess) e = cudaMemset(f->tc_err, 0, 64);
   if (e != cudaSuccess) return cleanup(fno_cuda(e, "FNO allocation"));
   // the fused column kernel needs its plan in shared memory
   if (column_fwd_mix_smem(n) <= 220 * 1024 && row_dft_smem(n, m) <= 220 * 1024 && 2 * m <= 64 &&
@@ -1057,6 +1145,7 @@ ttsh_status ttsh_fno_loss_grad(ttsh_fno* f, const float* x, const float* target,
     FNO_CUDA(cudaMemcpyAsync(grad_host, f->grad, f->nparams * 4, cudaMemcpyDeviceToHost, f->stream), "get grad");
   }
   FNO_CUDA(cudaStreamSynchronize(f->stream), "loss_grad");
+  if ((st = check_tc(f)) != TTSH_OK) return st;
   if (loss) *loss = l;
   return TTSH_OK;
 }
