@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(128) pointwise_tc_kernel(PwArgs a) {
   __shared__ __align__(1024) uint8_t sa[kTcRows * CW * 2];
   __shared__ __align__(1024) uint8_t sb[CW * CW * 2];
   __shared__ float sbias[CW];
+  __shared__ float stile[4 * 32 * 33];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -240,26 +241,43 @@ __global__ void __launch_bounds__(128) pointwise_tc_kernel(PwArgs a) {
                    "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                  : "r"(tmem + ((uint32_t)(warp * 32) << 16)));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const long long p = row0 + warp * 32 + lane;
-    if (p < a.P) {
+    // Epilogue through a padded 32 x 33 shared tile per warp: the warp's 32 rows are one
+    // contiguous 4 KB block in global memory, so the residual is read and the results are
+    // written with consecutive lanes on consecutive addresses; each thread then works on its
+    // own row (the accumulator layout) without bank conflicts.
+    float* tile = stile + warp * 32 * 33;
+    const long long p0 = row0 + warp * 32;
+    const int nrows = a.P - p0 >= 32 ? 32 : (a.P - p0 > 0 ? (int)(a.P - p0) : 0);
+    for (int j = 0; j < nrows; ++j) tile[j * 33 + lane] = a.add[(p0 + j) * CW + lane];
+    __syncwarp();
+    float v[CW];
 #pragma unroll
-      for (int o = 0; o < CW; o += 4) {
-        const long long idx = p * CW + o;
-        const float4 ad = *reinterpret_cast<const float4*>(a.add + idx);
-        float v[4] = {__uint_as_float(r[o]) + ad.x, __uint_as_float(r[o + 1]) + ad.y,
-                      __uint_as_float(r[o + 2]) + ad.z, __uint_as_float(r[o + 3]) + ad.w};
-        if (EPI != EPI_BWD)
-          for (int q = 0; q < 4; ++q) v[q] += sbias[o + q];
-        *reinterpret_cast<float4*>(a.out + idx) = make_float4(v[0], v[1], v[2], v[3]);
-        if (EPI == EPI_FWD) {
-          const float h0 = gelu(v[0]), h1 = gelu(v[1]), h2 = gelu(v[2]), h3 = gelu(v[3]);
-          *reinterpret_cast<float4*>(a.h + idx) = make_float4(h0, h1, h2, h3);
-          *reinterpret_cast<__nv_bfloat162*>(a.hb + idx) = __floats2bfloat162_rn(h0, h1);
-          *reinterpret_cast<__nv_bfloat162*>(a.hb + idx + 2) = __floats2bfloat162_rn(h2, h3);
-        } else if (EPI == EPI_FWD_LAST) {
-          *reinterpret_cast<float4*>(a.h + idx) = make_float4(v[0], v[1], v[2], v[3]);
-        }
+    for (int o = 0; o < CW; ++o) {
+      v[o] = __uint_as_float(r[o]) + tile[lane * 33 + o];
+      if (EPI != EPI_BWD) v[o] += sbias[o];
+    }
+    __syncwarp();
+    if (a.out) {
+#pragma unroll
+      for (int o = 0; o < CW; ++o) tile[lane * 33 + o] = v[o];
+      __syncwarp();
+      for (int j = 0; j < nrows; ++j) a.out[(p0 + j) * CW + lane] = tile[j * 33 + lane];
+      __syncwarp();
+    }
+    if (EPI != EPI_BWD) {
+#pragma unroll
+      for (int o = 0; o < CW; ++o) tile[lane * 33 + o] = EPI == EPI_FWD ? gelu(v[o]) : v[o];
+      __syncwarp();
+      if (a.h)
+        for (int j = 0; j < nrows; ++j) a.h[(p0 + j) * CW + lane] = tile[j * 33 + lane];
+      if (EPI == EPI_FWD && a.hb) {
+        // two rows per warp instruction: lanes 0-15 row j, 16-31 row j + 1, two channels each
+        const int half = lane >> 4, c2 = (lane & 15) * 2;
+        for (int j = half; j < nrows; j += 2)
+          *reinterpret_cast<__nv_bfloat162*>(a.hb + (p0 + j) * CW + c2) =
+              __floats2bfloat162_rn(tile[j * 33 + c2], tile[j * 33 + c2 + 1]);
       }
+      __syncwarp();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");   // accumulator read before reuse
   }
@@ -841,7 +859,7 @@ ttsh_status forward_impl(ttsh_fno* f, const float* x, int B, float* out, const f
     a.Bt = f->wbf + f->boff_Wt[l];
     a.bias = f->theta + f->off_b[l];
     a.add = f->s;
-    a.out = f->z[l];
+    a.out = target ? f->z[l] : nullptr;   // pre-activations are kept only for the backward pass
     a.h = f->h[l + 1];
     a.hb = l + 1 < L ? f->hb[l + 1] : nullptr;
     a.P = P;
