@@ -8,10 +8,11 @@
 //
 // Arithmetic: learned weights are held as FP32 master copies and used in BF16 by the kernels;
 // every product accumulates in FP32.  The channel-mixing layers (h W, and dz W^T in the
-// backward pass) run on the tensor cores (mma.sync m16n8k16 BF16 -> FP32, fused bias /
-// residual / GELU epilogue).  The transforms restricted to the kept modes are exact DFT
-// matrices applied by an FP32 batched GEMM (2m x n per row and per column, cheaper than a full
-// FFT when m << n), and the per-mode complex mixing reads BF16 weights with FP32 sums.
+// backward pass) run on the 5th-generation tensor cores (tcgen05.mma BF16 -> FP32 in tensor
+// memory, fused bias / residual / GELU epilogue).  The transforms restricted to the kept
+// modes are exact DFT matrices (2m x n per row and per column, cheaper than a full FFT when
+// m << n) applied by dedicated FP32 kernels, and the per-mode complex mixing reads BF16
+// weights with FP32 sums.
 // Gradients use fixed-order partial sums, so repeated calls give identical bits.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
