@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import ttsh_inputs as ti  # noqa: E402
-from paper_2304_03306_gb300 import sharding as S  # noqa: E402
+from paper_2304_03306_gb300 import sharding as shd  # noqa: E402
 
 METRIC = "grid-point-steps/s FP32 vs FP64 on 1 GB300; surrogate speedup at ≤2% error"
 UNIT = "grid-point-steps/s"
@@ -233,7 +233,7 @@ def run_ours(args, rank, world, local_rank):
         tdist.init_process_group("nccl", device_id=dev)
 
     def barrier():
-        S.barrier(dev)
+        shd.barrier(dev)
 
     w = ti.WORKLOADS[args.workload]
     n, dx = w["n"], w["dx"]
@@ -270,7 +270,7 @@ def run_ours(args, rank, world, local_rank):
         return sum(a.elapsed_time(b) for a, b in evs) / 1e3
 
     def max_over_ranks(x):
-        return S.max_over_ranks(x, device=dev)
+        return shd.max_over_ranks(x, device=dev)
 
     # ---- float32 (headline) ----
     dom = ttsh.Domain(mask, n, dx, precision=32, stream=stream.cuda_stream)
@@ -335,7 +335,7 @@ def run_ours(args, rank, world, local_rank):
         sweep = ti.sweep_domains()
         # the 48 domains are split over the ranks (cost-balanced, no collective); each rank
         # steps its share as one batch
-        mine = S.shard([d["n"] ** 2 for d in sweep], rank, world)
+        mine = shd.shard([d["n"] ** 2 for d in sweep], rank, world)
         objs = []
         for dspec in (sweep[i] for i in mine):
             o = ttsh.Domain(dspec["mask"], dspec["n"], dspec["dx"], precision=32, stream=stream.cuda_stream)
