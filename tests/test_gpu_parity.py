@@ -112,6 +112,50 @@ def test_bench_workload_512(T, prec):
     check_fields(dom, s, TOL[prec])
 
 
+def test_fp64_workload_64_over_2000_steps(T):
+    """The 64^2 FP64 configuration (circle R = 5.2, dx = 0.25, noise 0.01, seed 1) over its
+    full 2000 steps against the oracle."""
+    w = ti.WORKLOADS["circle64_fp64"]
+    dom, p, K, s = setup(T, w["n"], w["dx"], w["radius"], 64, w["seed"], amp=0.01)
+    dom.step(2000)
+    s = O.run(s, K, p, 2000)
+    check_fields(dom, s, 1e-12)
+    w_hat, _ = dom.spectral_state()
+    assert rel(w_hat, half_layout(s.w_hat)) <= 1e-12
+
+
+def test_fp64_workload_64_reaches_the_stationary_vortex(T):
+    """Long run of the same configuration: a single stationary vortex (P8) - the state stops
+    changing, the velocity is nearly azimuthal (Psi > 0.8) and |omega| peaks at the centre."""
+    w = ti.WORKLOADS["circle64_fp64"]
+    n, dx = w["n"], w["dx"]
+    dom, p, K, s = setup(T, n, dx, w["radius"], 64, w["seed"], amp=0.01)
+    dom.step(30000)
+    w0, _ = dom.spectral_state()
+    dom.step(1)
+    w1, _ = dom.spectral_state()
+    assert np.linalg.norm(w1 - w0) / np.linalg.norm(w1) < 1e-9
+    d = dom.diagnostics()
+    assert d["psi"] > 0.8
+    _, _, om = dom.fields()
+    X, Y = ti.grid_coords(n, dx)
+    iy, ix = np.unravel_index(np.argmax(np.abs(om)), om.shape)
+    assert np.hypot(X[iy, ix], Y[iy, ix]) <= 2 * dx
+
+
+def test_fp32_and_fp64_series_agree_on_the_512_workload(T):
+    """The 512^2 configuration's energy and order-parameter series in both precisions (before
+    any chaotic amplification the FP32 run tracks the FP64 one)."""
+    w = ti.WORKLOADS["circle512"]
+    series = {}
+    for prec in (32, 64):
+        dom, _, _, _ = setup(T, w["n"], w["dx"], w["radius"], prec, w["seed"], amp=0.01)
+        series[prec] = dom.record(2000, 10)
+    a, b = series[32], series[64]
+    assert np.array_equal(a[:, 0], b[:, 0])
+    assert rel(a[:, 1], b[:, 1]) <= 1e-4 and rel(a[:, 3], b[:, 3]) <= 1e-4
+
+
 @pytest.mark.parametrize("prec", [32, 64])
 def test_2048_few_steps(T, prec):
     w = ti.WORKLOADS["circle2048_turbulent"]
