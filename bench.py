@@ -365,7 +365,7 @@ def run_ours(args, rank, world, local_rank):
         kl, il = 8, 10
         dl = ttsh.Domain(mask, n, dx, precision=32, stream=stream.cuda_stream)
         dl.set_velocity(vx0, vy0)
-        dl.set_plan(plan32["row_variant"], plan32["col_variant"], plan32["pdl"])
+        dl.set_plan(plan32["row_variant"], plan32["col_variant"], plan32["launch_mode"])
         dl.step(200)
         w0, m0 = dl.spectral_state()
         u0 = np.concatenate([np.stack([w0.real, w0.imag], axis=-1).reshape(-1), m0])
@@ -424,7 +424,7 @@ def run_ours(args, rank, world, local_rank):
         hx[:], hy[:] = vx0, vy0
         ox, oy, ow = pin((n, n)), pin((n, n)), pin((n, n))
         de = ttsh.Domain(mask, n, dx, precision=32, stream=stream.cuda_stream)
-        de.set_plan(plan32["row_variant"], plan32["col_variant"], plan32["pdl"])
+        de.set_plan(plan32["row_variant"], plan32["col_variant"], plan32["launch_mode"])
         lib = ttsh.load_library()
         P = lambda a: a.ctypes.data_as(ttsh._D)
 

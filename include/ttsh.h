@@ -189,19 +189,25 @@ ttsh_status ttsh_time_kernels(ttsh_domain* d, int32_t iters, double* ms);
  * restored) and selects the fastest row and column variant.  plan (8 int32, may be NULL):
  * {row variant, column variant, rows per block, row points per thread, column points per
  * thread, number of row variants, number of column variants, launch mode}.  ttsh_set_plan
- * selects variants by index (TTSH_E_INVALID if out of range).  After choosing the variants
- * ttsh_autotune also times whole steps (graphs of up to 64 steps, state restored) in both
- * launch modes and keeps the faster. */
+ * selects variants by index (TTSH_E_INVALID if out of range).  ttsh_autotune times each row
+ * variant with its G tile staged both ways (see ttsh_set_launch_mode), keeps the fastest
+ * (variant, staging) pair, and then times whole steps (graphs of up to 64 steps, state
+ * restored) with and without programmatic dependent launch and keeps the faster. */
 ttsh_status ttsh_autotune(ttsh_domain* d, int32_t iters, int32_t* plan);
 ttsh_status ttsh_get_plan(ttsh_domain* d, int32_t* plan);
 ttsh_status ttsh_set_plan(ttsh_domain* d, int32_t row_variant, int32_t col_variant);
 
-/* Launch mode of the step kernels: 0 = ordinary stream-ordered launches; 1 = programmatic
- * dependent launches, where a pass may start (copy its twiddle tables and mask rows) while
- * the previous pass is still running and waits on the device (griddepcontrol.wait) before it
- * reads anything that pass wrote.  Results are bit-identical in both modes; other values ->
- * TTSH_E_INVALID.  The paper has no counterpart: this is a scheduling option. */
-ttsh_status ttsh_set_launch_mode(ttsh_domain* d, int32_t pdl);
+/* Launch mode of the step kernels, a bit set:
+ *   bit 0  programmatic dependent launches: a pass may start (copy its twiddle tables and
+ *          mask rows) while the previous pass is still running and waits on the device
+ *          (griddepcontrol.wait) before it reads anything that pass wrote;
+ *   bit 1  the row pass loads its G tile with the tensor-memory accelerator (one 2D tile load
+ *          per field, completion on an mbarrier with a bounded wait) instead of cp.async,
+ *          where the tile allows it (N <= 512 and a row segment of R complex values a
+ *          multiple of 16 bytes); elsewhere cp.async is used whatever the bit.
+ * Results are bit-identical in every mode; values outside [0, 3] -> TTSH_E_INVALID.  The
+ * paper has no counterpart: these are scheduling options. */
+ttsh_status ttsh_set_launch_mode(ttsh_domain* d, int32_t mode);
 
 /* Advance a caller-owned state by nsteps steps of Algorithm 1 without allocating any device
  * memory (the paper has no counterpart: this is a library convenience).  It is meant for

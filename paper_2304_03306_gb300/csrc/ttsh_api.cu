@@ -46,7 +46,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 struct Layout {
-  size_t what, vmean, K, G, Rr, tw, real, part, colhist, bad, out, save, rec, recctl, total;
+  size_t what, vmean, K, G, Rr, tw, real, part, colhist, bad, out, save, rec, recctl, err, total;
 };
 
 Layout layout_for(int n, size_t elt) {
@@ -73,6 +73,7 @@ Layout layout_for(int n, size_t elt) {
   L.save = take(H * NK * 2 * elt + 64);   // state copy kept by ttsh_time_kernels
   L.rec = take((size_t)n * ttsh::kDiagQ * sizeof(double));   // time-series partials (<= n row blocks)
   L.recctl = take(64);                                        // time-series write position
+  L.err = take(64);                                           // device status word
   static_assert(sizeof(ttsh::RecCtl) <= 64, "RecCtl must fit its region");
   L.total = off;
   return L;
@@ -108,6 +109,53 @@ std::vector<T> twiddles(int n) {
     tw[2 * m + 1] = (T)(double)(-sinl(ang));
   }
   return tw;
+}
+
+// cuTensorMapEncodeTiled from the driver (resolved once through the runtime; no link-time
+// dependency on the driver library).
+typedef CUresult (*TmapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TmapEncodeFn tmap_encoder() {
+  static const TmapEncodeFn fn = []() -> TmapEncodeFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return reinterpret_cast<TmapEncodeFn>(p);
+  }();
+  return fn;
+}
+
+// Tensor maps of G ([3 (N/4+1)] rows of 2N scalars, row pitch N complex) for the row pass's
+// TMA loads, one per row-block height R = 1, 2, 4 (box: 2R scalars x N/4+1 rows).  A shape
+// the TMA cannot take (more than 256 rows in a box, or an R-row segment that is not a
+// multiple of 16 bytes) leaves tma_ok = 0 and the row pass uses cp.async instead.
+void init_tensor_maps(ttsh::DomainDev& v, int n, size_t elt) {
+  const int H = n / 4 + 1;
+  for (int i = 0; i < 3; ++i) {
+    v.tma_ok[i] = 0;
+    memset(&v.tmapG[i], 0, sizeof(v.tmapG[i]));
+  }
+  const TmapEncodeFn fn = tmap_encoder();
+  if (!fn || H > 256) return;
+  const size_t cb = 2 * elt;
+  for (int i = 0; i < 3; ++i) {
+    const int R = 1 << i;
+    if ((R * cb) % 16 != 0 || n % R != 0) continue;
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * n, (cuuint64_t)3 * H};
+    const cuuint64_t strides[1] = {(cuuint64_t)n * cb};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * R), (cuuint32_t)H};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = fn(&v.tmapG[i], elt == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                          v.G, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    v.tma_ok[i] = r == CUDA_SUCCESS ? 1 : 0;
+  }
 }
 
 }  // namespace
@@ -288,6 +336,17 @@ ttsh_status build_graph(ttsh_domain* d) {
   return TTSH_OK;
 }
 
+// Device status word: a kernel whose bounded wait ran out set it; report it once.
+ttsh_status check_status(ttsh_domain* d) {
+  int h = 0;
+  TTSH_CUDA(cudaMemcpy(&h, d->dev.err, sizeof(int), cudaMemcpyDeviceToHost), "read status word");
+  if (h) {
+    cudaMemset(d->dev.err, 0, sizeof(int));
+    return fail(TTSH_E_TIMEOUT, "a bounded wait in a kernel ran out (results of the affected steps are not valid)");
+  }
+  return TTSH_OK;
+}
+
 ttsh_status project_staged(ttsh_domain* d) {
   ttsh_status st = run_row(d, ttsh::K_ROW_FWD_VEL, d->stream);
   if (st != TTSH_OK) return st;
@@ -426,8 +485,12 @@ int domain_clone(const ttsh_domain* src, ttsh_domain** out) {
   v.out = reinterpret_cast<double*>(base + d->lay.out);
   v.rec = nullptr;
   v.recctl = nullptr;
+  v.err = reinterpret_cast<int*>(base + d->lay.err);
+  init_tensor_maps(v, d->n, d->elt);
   const size_t NN = (size_t)d->n * d->n;
   const size_t wbytes = (size_t)d->H * d->NK * 2 * d->elt;
+  e = cudaMemsetAsync(v.err, 0, 64, d->stream);
+  if (e != cudaSuccess) return cleanup(cuda_fail(e, "status word"));
   e = cudaMemcpyAsync(v.K, src->dev.K, NN * d->elt, cudaMemcpyDeviceToDevice, d->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.tw, src->dev.tw, (size_t)d->n * 2 * d->elt, cudaMemcpyDeviceToDevice, d->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.what, src->dev.what, wbytes, cudaMemcpyDeviceToDevice, d->stream);
@@ -774,6 +837,16 @@ ttsh_status ttsh_create_domain(const uint8_t* mask, const ttsh_params* p, void* 
   v.cx = 0.0;
   v.cy = 0.0;
   v.n = p->n;
+  v.rec = nullptr;
+  v.recctl = nullptr;
+  v.pdl = 0;
+  v.use_tma = 0;
+  v.err = reinterpret_cast<int*>(base + d->lay.err);
+  init_tensor_maps(v, d->n, d->elt);
+  {
+    cudaError_t e = cudaMemsetAsync(v.err, 0, 64, d->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(e, "status word"));
+  }
 
   const size_t NN = (size_t)d->n * d->n;
   cudaStream_t s = d->stream;
@@ -1050,6 +1123,7 @@ ttsh_status ttsh_diagnostics(ttsh_domain* d, ttsh_diag* out, double* spectrum, i
   out->nonfinite = (int32_t)h[4] + bad;
   out->reserved = 0;
   for (int i = 0; i < nbins; ++i) spectrum[i] = i < nb_dev ? h[8 + i] : 0.0;
+  if ((st = check_status(d)) != TTSH_OK) return st;
   if (out->nonfinite) return fail(TTSH_E_NONFINITE, "state holds non-finite values");
   return TTSH_OK;
 }
@@ -1073,15 +1147,19 @@ ttsh_status ttsh_autotune(ttsh_domain* d, int32_t iters, int32_t* plan) {
   if (iters < 1 || iters > 100000) return fail(TTSH_E_INVALID, "iters must be in [1, 100000]");
   ttsh_status st = save_state(d);
   if (st != TTSH_OK) return st;
-  const int pdl0 = d->dev.pdl;
+  const int pdl0 = d->dev.pdl, tma0 = d->dev.use_tma;
   d->dev.pdl = 0;   // variants are timed as plain back-to-back launches
   double best = 1e300;
-  int br = 0, bc = 0;
+  int br = 0, bc = 0, btma = 0;
   for (int i = 0; i < d->ops.n_row_variants; ++i) {
-    double t;
-    if ((st = time_launches(d, d->ops.row_step[i].fn, iters, &t)) != TTSH_OK) return st;
-    if (t < best) { best = t; br = i; }
+    for (int tma = 0; tma < 2; ++tma) {   // G tile by cp.async, then by TMA (where the tile allows)
+      d->dev.use_tma = tma;
+      double t;
+      if ((st = time_launches(d, d->ops.row_step[i].fn, iters, &t)) != TTSH_OK) return st;
+      if (t < best) { best = t; br = i; btma = tma; }
+    }
   }
+  d->dev.use_tma = btma;
   best = 1e300;
   for (int i = 0; i < d->ops.n_col_variants; ++i) {
     double t;
@@ -1089,25 +1167,27 @@ ttsh_status ttsh_autotune(ttsh_domain* d, int32_t iters, int32_t* plan) {
     if (t < best) { best = t; bc = i; }
   }
   d->dev.pdl = pdl0;
+  d->dev.use_tma = tma0;
   if ((st = restore_state(d)) != TTSH_OK) return st;
   if ((st = ttsh_set_plan(d, br, bc)) != TTSH_OK) return st;
   // launch mode: whole steps (row then column pass) with and without programmatic
   // dependent launch; keep the faster
   double t_mode[2];
   for (int pdl = 0; pdl < 2; ++pdl) {
-    if ((st = ttsh_set_launch_mode(d, pdl)) != TTSH_OK) return st;
+    if ((st = ttsh_set_launch_mode(d, pdl | (btma << 1))) != TTSH_OK) return st;
     if ((st = save_state(d)) != TTSH_OK) return st;
     if ((st = time_steps(d, iters, &t_mode[pdl])) != TTSH_OK) return st;
     if ((st = restore_state(d)) != TTSH_OK) return st;
   }
-  if ((st = ttsh_set_launch_mode(d, t_mode[1] < t_mode[0] ? 1 : 0)) != TTSH_OK) return st;
+  if ((st = ttsh_set_launch_mode(d, (t_mode[1] < t_mode[0] ? 1 : 0) | (btma << 1))) != TTSH_OK) return st;
   return ttsh_get_plan(d, plan);
 }
 
-ttsh_status ttsh_set_launch_mode(ttsh_domain* d, int32_t pdl) {
+ttsh_status ttsh_set_launch_mode(ttsh_domain* d, int32_t mode) {
   if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
-  if (pdl != 0 && pdl != 1) return fail(TTSH_E_INVALID, "launch mode must be 0 or 1");
-  if (pdl != d->dev.pdl) {
+  if (mode < 0 || mode > 3) return fail(TTSH_E_INVALID, "launch mode must be in [0, 3]");
+  const int pdl = mode & 1, tma = (mode >> 1) & 1;
+  if (pdl != d->dev.pdl || tma != d->dev.use_tma) {
     if (d->graph) {
       cudaGraphExecDestroy(d->graph);
       d->graph = nullptr;
@@ -1115,6 +1195,7 @@ ttsh_status ttsh_set_launch_mode(ttsh_domain* d, int32_t pdl) {
     }
     drop_record_graph(d);
     d->dev.pdl = pdl;
+    d->dev.use_tma = tma;
   }
   return TTSH_OK;
 }
@@ -1129,7 +1210,7 @@ ttsh_status ttsh_get_plan(ttsh_domain* d, int32_t* plan) {
     plan[4] = d->ops.col_step[d->cv].pe;
     plan[5] = d->ops.n_row_variants;
     plan[6] = d->ops.n_col_variants;
-    plan[7] = d->dev.pdl;
+    plan[7] = d->dev.pdl | (d->dev.use_tma << 1);
   }
   return TTSH_OK;
 }
@@ -1349,7 +1430,9 @@ ttsh_status ttsh_dumbbell_order(ttsh_domain* d, const double* centres, double ra
 
 ttsh_status ttsh_synchronize(ttsh_domain* d) {
   if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
-  return sync(d, "synchronize");
+  ttsh_status st = sync(d, "synchronize");
+  if (st != TTSH_OK) return st;
+  return check_status(d);
 }
 
 int64_t ttsh_step_count(const ttsh_domain* d) { return d ? d->steps : -1; }

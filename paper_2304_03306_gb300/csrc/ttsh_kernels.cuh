@@ -36,6 +36,8 @@
 // once, one wait), so the transform stages never wait on global memory.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the tensor-map descriptor of the TMA loads)
+
 #include "ttsh_fft.cuh"
 
 namespace ttsh {
@@ -69,6 +71,8 @@ struct Args {
   double* part;         // per-block diagnostic partial sums
   double* rec;          // per-block time-series partials of a recorded step, or null
   RecCtl* recctl;       // with rec: where the column pass appends the step's sample
+  int* err;             // device status word: 1 = a bounded wait in a kernel ran out
+  int tma;              // 1: the row pass loads its G tile with the tensor-memory accelerator
   T a, b, lam, gv, gw, dt, dk, mean_decay;   // mean_decay = exp((a - 1) dt)
   double dx, cx, cy;    // grid spacing and the psi centre
 };
@@ -79,9 +83,11 @@ enum ColMode { COL_STEP = 0, COL_PROLOGUE = 1, COL_PROJECT = 2, COL_MASK = 3, CO
 
 constexpr int kDiagQ = 5;   // per-block partials: sum|v|^2, sum w^2, sum|e_th.v|, sum|v|, #nonfinite
 constexpr int kSmemLimit = 220 * 1024;
-constexpr int kRecSmem = 32 * kDiagQ * 8;   // static shared memory of the time-series reduction
+constexpr int kRecSmem = 32 * kDiagQ * 8 + 16;   // static shared memory: time-series reduction, TMA barrier
+constexpr long long kTmaSpin = 1ll << 24;        // bound on the TMA completion wait (polls)
 
 __host__ __device__ constexpr int align16(int v) { return (v + 15) / 16 * 16; }
+__host__ __device__ constexpr int align128(int v) { return (v + 127) / 128 * 128; }
 
 template <int KIND> __host__ __device__ constexpr int row_inv_fields() {
   return KIND == ROW_STEP ? 3 : KIND == ROW_INV_FIELDS ? 3 : KIND == ROW_INV_DIAG ? 3
@@ -125,7 +131,10 @@ struct RowGeo {
   static constexpr int OFF_STAB = align16(TwTab<T, N>::ENTRIES * CB);
   // every region starts on a 16-byte boundary (16-byte cp.async destinations)
   static constexpr int BUF_BYTES = align16(F * R * LPR * CB);
-  static constexpr int GIN_BYTES = align16(NPL * H * R * CB);
+  // staged G tile: plane f at OFF_GIN + f * GPS ([mx][r] inside a plane); planes start on
+  // 128-byte boundaries, as tensor-memory-accelerator destinations must
+  static constexpr int GPS = align128(H * R * CB);
+  static constexpr int GIN_BYTES = NPL * GPS;
   static constexpr int KS_BYTES = KIND == ROW_STEP ? align16(R * N * (int)sizeof(T)) : 0;
   static constexpr int RED_BYTES = KIND == ROW_INV_DIAG ? kDiagQ * 1024 * 8 : 0;
   static constexpr bool STAGE_K = KS_BYTES > 0 && TW_BYTES + BUF_BYTES + KS_BYTES + RED_BYTES <= kSmemLimit;
@@ -139,19 +148,23 @@ struct RowGeo {
   static constexpr bool SEPARATE = KIND == ROW_STEP && sizeof(T) == 4 && STAGE_K &&
       TW_BYTES + 2 * BUF_BYTES + (STAGE_G ? GIN_BYTES : 0) + KS_BYTES <= kSmemLimit;
   static constexpr int OFF_BUF = TW_BYTES;
-  static constexpr int OFF_GIN = OFF_BUF + BUF_BYTES;
+  static constexpr int OFF_GIN = align128(OFF_BUF + BUF_BYTES);
   static constexpr int OFF_KS = OFF_GIN + (STAGE_G ? GIN_BYTES : 0);
   static constexpr int OFF_RED = OFF_KS + (STAGE_K ? KS_BYTES : 0);
   static constexpr int OFF_FWD = OFF_RED + RED_BYTES;
-  static constexpr int SMEM = OFF_FWD + (SEPARATE ? BUF_BYTES : 0);
+  // + 128: the kernel aligns its dynamic shared-memory base to 128 bytes
+  static constexpr int SMEM = OFF_FWD + (SEPARATE ? BUF_BYTES : 0) + 128;
+  // the G tile can come by TMA: one box of R rows x (N/4+1) columns per plane (at most 256
+  // columns in a box; a row segment of R complex values a multiple of 16 bytes)
+  static constexpr bool TMA_OK = STAGE_G && H <= 256 && (R * CB) % 16 == 0;
   static constexpr int NT = cmax(64, cmin(1024, F * R * TT));
   static constexpr int SEG = R * CB;                        // bytes per (plane, mx) segment
   static constexpr int CHUNK = SEG % 16 == 0 ? 16 : 8;
   static constexpr bool VALID = SMEM + (KIND == ROW_STEP ? kRecSmem : 0) <= 227 * 1024 && N % R == 0 &&
                                 R <= N && TT <= 1024 && NT % TT == 0;
-  static_assert(OFF_BUF % 16 == 0 && OFF_GIN % 16 == 0 && OFF_KS % 16 == 0 && OFF_RED % 16 == 0 &&
-                OFF_FWD % 16 == 0,
-                "row pass shared-memory regions must be 16-byte aligned");
+  static_assert(OFF_BUF % 16 == 0 && OFF_GIN % 128 == 0 && GPS % 128 == 0 && OFF_KS % 16 == 0 &&
+                OFF_RED % 16 == 0 && OFF_FWD % 16 == 0,
+                "row pass shared-memory regions must be 16-byte (G tile: 128-byte) aligned");
 };
 
 // Column-pass geometry and shared-memory plan.
@@ -272,8 +285,11 @@ __device__ __forceinline__ void record_sample(const Args<T>& A) {
 // ---------------------------------------------------------------------------------------
 // Row pass body (one block = rows [y0, y0 + R))
 // ---------------------------------------------------------------------------------------
+// tmapG: G as a 2D tensor [3 (N/4+1)][2N scalars] with a box of R rows x (N/4+1), a grid-
+// constant kernel parameter (used when A.tma is set; may be null otherwise).
 template <typename T, int N, int KIND, int R, int PEV>
-__device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned char* smem_raw) {
+__device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned char* smem_raw,
+                                         const CUtensorMap* tmapG) {
   using Geo = RowGeo<T, N, KIND, R, PEV>;
   static_assert(Geo::VALID, "row pass tile does not fit");
   constexpr int L = Geo::L, M = Geo::M, H = Geo::H;
@@ -298,13 +314,43 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
   griddep_launch();
   griddep_wait();
   if constexpr (Geo::STAGE_G) {
-    constexpr int CPS = Geo::SEG / Geo::CHUNK;   // chunks per segment
-    constexpr int PLANE0 = 0;
-    for (int i = tid; i < Geo::NPL * H * CPS; i += NT) {
-      const int c = i % CPS;
-      const int t = i / CPS;                     // t = pl * H + kx
-      const char* src = reinterpret_cast<const char*>(A.G + ((size_t)(PLANE0 * H + t)) * N + y0) + c * Geo::CHUNK;
-      cp_async<Geo::CHUNK>(reinterpret_cast<char*>(gin + (size_t)t * R) + c * Geo::CHUNK, src);
+    bool via_tma = false;
+    if constexpr (Geo::TMA_OK) via_tma = A.tma != 0 && tmapG != nullptr;
+    if (via_tma) {
+      // one tensor-memory-accelerator load per plane: box (R consecutive y) x (all N/4+1
+      // columns) of G, landing as [mx][r]; completion counted in bytes on an mbarrier
+      __shared__ __align__(8) unsigned long long tma_bar;
+      const unsigned bar = (unsigned)__cvta_generic_to_shared(&tma_bar);
+      if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      }
+      __syncthreads();
+      if (tid == 0) {
+        constexpr unsigned bytes = (unsigned)(Geo::NPL * H * R * Geo::CB);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        for (int pl = 0; pl < Geo::NPL; ++pl) {
+          const unsigned dst = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char*>(gin) + pl * Geo::GPS);
+          const int x = 2 * y0, y = pl * H;   // scalar column (16-byte aligned: R * CB % 16 == 0), row
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+              ::"r"(dst), "l"(tmapG), "r"(x), "r"(y), "r"(bar) : "memory");
+        }
+      }
+      unsigned done = 0;
+      for (long long it = 0; it < kTmaSpin && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(bar) : "memory");
+      if (!done) atomicExch(A.err, 1);
+    } else {
+      constexpr int CPS = Geo::SEG / Geo::CHUNK;   // chunks per (plane, mx) segment
+#pragma unroll
+      for (int pl = 0; pl < Geo::NPL; ++pl) {
+        const char* gsrc = reinterpret_cast<const char*>(A.G + (size_t)pl * H * N + y0);
+        char* gdst = reinterpret_cast<char*>(gin) + pl * Geo::GPS;
+        for (int i = tid; i < H * CPS; i += NT)   // i = kx * CPS + c: the plane is [mx][r]
+          cp_async<Geo::CHUNK>(gdst + i * Geo::CHUNK, gsrc + (size_t)(i / CPS) * N * Geo::CB + (i % CPS) * Geo::CHUNK);
+      }
     }
   }
   cp_async_wait_all();   // tables and staged inputs
@@ -320,7 +366,7 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
       cplx<T> X = mk<T>(0, 0), Xm = mk<T>(0, 0);
       const int km = L - k;
       if constexpr (Geo::STAGE_G) {
-        const cplx<T>* src = gin + (size_t)f * H * R + r;
+        const cplx<T>* src = gin + (size_t)f * (Geo::GPS / Geo::CB) + r;
         if (k <= M) X = src[k * R];
         if (km <= M) Xm = src[km * R];
       } else {
@@ -627,11 +673,20 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
 // ---------------------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------------------
+// Dynamic shared memory re-based to a 128-byte boundary (TMA destinations need it; the row
+// geometry reserves the slack).
+__device__ __forceinline__ unsigned char* smem_base128(unsigned char* raw) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(raw);
+  return raw + ((128u - (a & 127u)) & 127u);
+}
+
+// The tensor map is a separate grid-constant parameter so that its address can be handed to
+// the TMA while the argument block stays an ordinary by-value parameter.
 template <typename T, int N, int KIND, int R, int PEV>
 __global__ void __launch_bounds__(RowGeo<T, N, KIND, R, PEV>::NT)
-row_kernel(Args<T> A) {
+row_kernel(Args<T> A, const __grid_constant__ CUtensorMap tmapG) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  row_body<T, N, KIND, R, PEV>(A, blockIdx.x, smem_raw);
+  row_body<T, N, KIND, R, PEV>(A, blockIdx.x, smem_base128(smem_raw), &tmapG);
 }
 
 template <typename T, int N, int MODE, int PEV>
@@ -652,8 +707,8 @@ template <typename T, int N, int KIND, int R, int PEV>
 __global__ void __launch_bounds__(RowGeo<T, N, KIND, R, PEV>::NT)
 row_kernel_batched(const Args<T>* __restrict__ args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Args<T> A = args[blockIdx.y];
-  row_body<T, N, KIND, R, PEV>(A, blockIdx.x, smem_raw);
+  const Args<T> A = args[blockIdx.y];   // tma is 0 in packed argument blocks
+  row_body<T, N, KIND, R, PEV>(A, blockIdx.x, smem_base128(smem_raw), nullptr);
 }
 
 template <typename T, int N, int MODE, int PEV>

@@ -2,6 +2,7 @@
 // and the per-precision kernel translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -26,6 +27,12 @@ struct DomainDev {
   double cx, cy;   // centre for the order parameter
   int n;
   int pdl;         // launch the step kernels with programmatic dependent launch
+  int use_tma;     // let the row step kernel load its G tile with the TMA (where tma_ok)
+  int* err;        // device status word (bounded waits that ran out)
+  // G as a 2D tensor for the row pass's TMA loads, one map per row-block height R = 1, 2, 4
+  // (tma_ok[i] = 0 where the shape does not allow it or the map could not be made)
+  CUtensorMap tmapG[3];
+  int tma_ok[3];
 };
 
 enum { K_ROW_STEP = 0, K_ROW_FWD_VEL = 1, K_ROW_FWD_MASK = 2, K_ROW_INV_FIELDS = 3,

@@ -24,6 +24,8 @@ static Args<T> make_args(const DomainDev& d) {
   a.part = d.part;
   a.rec = d.rec;
   a.recctl = static_cast<RecCtl*>(d.recctl);
+  a.err = d.err;
+  a.tma = 0;
   const double dk = 2.0 * 3.14159265358979323846264338327950288 / ((double)d.n * d.dx);
   a.a = (T)d.a;
   a.b = (T)d.b;
@@ -50,11 +52,11 @@ static cudaError_t set_smem(K kernel, int bytes, std::atomic<int>& done) {
 // Launch, optionally as a programmatic dependent launch: the kernel may start while the
 // previous kernel in the stream is still running; it waits (griddepcontrol.wait) before it
 // touches anything that kernel writes.
-template <typename T>
-static cudaError_t launch_k(void (*kernel)(Args<T>), int grid, int block, int smem, cudaStream_t s, bool pdl,
-                            const Args<T>& a) {
+template <typename... P, typename... V>
+static cudaError_t launch_k(void (*kernel)(P...), int grid, int block, int smem, cudaStream_t s, bool pdl,
+                            const V&... args) {
   if (!pdl) {
-    kernel<<<grid, block, smem, s>>>(a);
+    kernel<<<grid, block, smem, s>>>(args...);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
@@ -67,7 +69,7 @@ static cudaError_t launch_k(void (*kernel)(Args<T>), int grid, int block, int sm
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, a);
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 template <typename T, int N, int KIND, int R = default_rows<T, N>(), int PE = default_row_pe<T, N>()>
@@ -76,8 +78,17 @@ static cudaError_t launch_row_kind(const DomainDev& d, cudaStream_t s) {
   static std::atomic<int> done{0};
   cudaError_t e = set_smem(row_kernel<T, N, KIND, R, PE>, Geo::SMEM, done);
   if (e != cudaSuccess) return e;
-  return launch_k<T>(row_kernel<T, N, KIND, R, PE>, N / R, Geo::NT, Geo::SMEM, s, KIND == ROW_STEP && d.pdl,
-                     make_args<T>(d));
+  Args<T> a = make_args<T>(d);
+  CUtensorMap tm;
+  memset(&tm, 0, sizeof(tm));
+  constexpr int ri = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : -1;
+  if constexpr (Geo::TMA_OK && ri >= 0) {
+    if (d.use_tma && d.tma_ok[ri] && d.err) {
+      tm = d.tmapG[ri];
+      a.tma = 1;
+    }
+  }
+  return launch_k(row_kernel<T, N, KIND, R, PE>, N / R, Geo::NT, Geo::SMEM, s, KIND == ROW_STEP && d.pdl, a, tm);
 }
 
 template <typename T, int N, int MODE, int PE = default_col_pe<T, N>()>
@@ -88,8 +99,8 @@ static cudaError_t launch_col_mode(const DomainDev& d, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   // a recorded step adds one block that finishes the time-series sample
   const int extra = (MODE == COL_STEP && d.rec != nullptr) ? 1 : 0;
-  return launch_k<T>(col_kernel<T, N, MODE, PE>, Geo::H + extra, Geo::NT, Geo::SMEM, s, MODE == COL_STEP && d.pdl,
-                     make_args<T>(d));
+  return launch_k(col_kernel<T, N, MODE, PE>, Geo::H + extra, Geo::NT, Geo::SMEM, s, MODE == COL_STEP && d.pdl,
+                  make_args<T>(d));
 }
 
 template <typename T, int N>

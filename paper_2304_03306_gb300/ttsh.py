@@ -242,7 +242,7 @@ def ttsh_time_kernels(h, iters: int):
 
 
 _PLAN_KEYS = ("row_variant", "col_variant", "rows_per_block", "row_points_per_thread",
-              "col_points_per_thread", "n_row_variants", "n_col_variants", "pdl")
+              "col_points_per_thread", "n_row_variants", "n_col_variants", "launch_mode")
 
 
 def _plan_dict(buf):
@@ -265,8 +265,9 @@ def ttsh_set_plan(h, row_variant: int, col_variant: int):
     _check(load_library().ttsh_set_plan(h, int(row_variant), int(col_variant)))
 
 
-def ttsh_set_launch_mode(h, pdl: int):
-    _check(load_library().ttsh_set_launch_mode(h, int(pdl)))
+def ttsh_set_launch_mode(h, mode: int):
+    """mode bit 0: programmatic dependent launch; bit 1: TMA staging of the row pass's tile."""
+    _check(load_library().ttsh_set_launch_mode(h, int(mode)))
 
 
 def ttsh_batch_create(handles, stream: int | None = None):
@@ -499,10 +500,10 @@ class Domain:
     def plan(self) -> dict:
         return ttsh_get_plan(self.h)
 
-    def set_plan(self, row_variant: int, col_variant: int, pdl: int | None = None):
+    def set_plan(self, row_variant: int, col_variant: int, launch_mode: int | None = None):
         ttsh_set_plan(self.h, row_variant, col_variant)
-        if pdl is not None:
-            ttsh_set_launch_mode(self.h, pdl)
+        if launch_mode is not None:
+            ttsh_set_launch_mode(self.h, launch_mode)
 
     def time_kernels(self, iters: int):
         """Mean (row pass, column pass) launch durations in ms, state restored afterwards."""

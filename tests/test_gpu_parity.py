@@ -305,8 +305,8 @@ def test_graph_replay_equals_eager_launches(T):
     assert np.array_equal(a.spectral_state()[0], b.spectral_state()[0])
 
 
-@pytest.mark.parametrize("prec", [32, 64])
-def test_launch_modes_are_bit_identical(T, prec):
+@pytest.mark.parametrize("prec,mode", [(32, 1), (64, 1), (32, 2), (64, 2), (32, 3)])
+def test_launch_modes_are_bit_identical(T, prec, mode):
     n, dx = 64, 0.25
     mask = ti.circle_mask(n, dx, 5.2)
     vx, vy = ti.noise_velocity(mask, 12, 0.3)
@@ -314,8 +314,8 @@ def test_launch_modes_are_bit_identical(T, prec):
     b = T.Domain(mask, n, dx, precision=prec)
     for d in (a, b):
         d.set_velocity(vx, vy)
-    b.set_plan(0, 0, pdl=1)
-    assert b.plan()["pdl"] == 1 and a.plan()["pdl"] == 0
+    b.set_plan(0, 0, launch_mode=mode)
+    assert b.plan()["launch_mode"] == mode and a.plan()["launch_mode"] == 0
     a.step(300)          # graph replays plus eager steps
     b.step(300)
     assert np.array_equal(a.spectral_state()[0], b.spectral_state()[0])
@@ -323,7 +323,7 @@ def test_launch_modes_are_bit_identical(T, prec):
     assert np.array_equal(sa, sb)
     assert np.array_equal(a.spectral_state()[0], b.spectral_state()[0])
     with pytest.raises(T.TTSHError):
-        T.ttsh_set_launch_mode(a.h, 2)
+        T.ttsh_set_launch_mode(a.h, 4)
 
 
 def test_fp64_8192_is_unsupported(T):
