@@ -186,14 +186,20 @@ struct ColGeo {
   static constexpr int FB0 = cmax(NF, NI) >= 4 ? 4 : cmax(NF, NI);
   static constexpr int FB = (FIXED + FB0 * LP * CB <= kSmemLimit) ? FB0
                           : (FIXED + 2 * LP * CB <= kSmemLimit && FB0 >= 2) ? 2 : 1;
+  // forward inputs in one batch: the NF columns can come as bulk copies (contiguous in Rr)
+  // into an unpadded staging area that the first transform stage reads
+  static constexpr int STG_BYTES = NF * N * CB;
+  static constexpr bool BULK = NF > 0 && FB >= NF && FIXED + FB * LP * CB + STG_BYTES <= kSmemLimit;
   static constexpr int OFF_BUF = TW_BYTES;
   static constexpr int OFF_ACC = OFF_BUF + align16(FB * LP * CB);
   static constexpr int OFF_WS = OFF_ACC + ACC_BYTES;
-  static constexpr int OFF_S0 = OFF_WS + WS_BYTES;
+  static constexpr int OFF_STG = OFF_WS + WS_BYTES;
+  static constexpr int OFF_S0 = OFF_STG + (BULK ? STG_BYTES : 0);
   static constexpr int SMEM = OFF_S0 + 64;
   static constexpr int NT = cmax(64, cmin(1024, FB * TT));
   static constexpr bool VALID = SMEM <= 227 * 1024 && TT <= 1024 && NT % TT == 0;
-  static_assert(OFF_BUF % 16 == 0 && OFF_ACC % 16 == 0 && OFF_WS % 16 == 0 && OFF_S0 % 16 == 0,
+  static_assert(OFF_BUF % 16 == 0 && OFF_ACC % 16 == 0 && OFF_WS % 16 == 0 && OFF_STG % 16 == 0 &&
+                OFF_S0 % 16 == 0,
                 "column pass shared-memory regions must be 16-byte aligned");
 };
 
@@ -536,11 +542,43 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
     if constexpr (MODE == COL_STEP || MODE == COL_ADDW) {
       for (int j = tid; j < NK; j += NT) cp_async<CB>(ws + j, A.what + (size_t)kx * NK + j);
     }
+    if constexpr (Geo::BULK) {
+      // the NF columns (each N contiguous values of Rr) by bulk copies, completion counted
+      // in bytes on an mbarrier (bounded wait)
+      __shared__ __align__(8) unsigned long long col_bar;
+      const unsigned bar = (unsigned)__cvta_generic_to_shared(&col_bar);
+      if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      }
+      __syncthreads();
+      if (tid == 0) {
+        constexpr unsigned bytes = (unsigned)(NF * N * CB);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        for (int f = 0; f < NF; ++f) {
+          const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_raw + Geo::OFF_STG + (size_t)f * N * CB);
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                       ::"r"(dst), "l"(A.Rr + ((size_t)f * H + kx) * N), "r"((unsigned)(N * CB)), "r"(bar)
+                       : "memory");
+        }
+      }
+      unsigned done = 0;
+      for (long long it = 0; it < kTmaSpin && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done) : "r"(bar) : "memory");
+      if (!done && A.err) atomicExch(A.err, 1);
+    }
     for (int f0 = 0; f0 < NF; f0 += FB) {
       const int nb = cmin(FB, NF - f0);
-      stage_columns(f0, nb);
-      cp_async_wait_all();
-      fft_batch<T, N, PE, -1, NT, N>(buf, nb, tw, stab);
+      if constexpr (Geo::BULK) {
+        const cplx<T>* stg = reinterpret_cast<const cplx<T>*>(smem_raw + Geo::OFF_STG);
+        cp_async_wait_all();   // tables, state column
+        fft_batch<T, N, PE, -1, NT, N>(buf, nb, tw, stab, [&](int bt, int m) { return stg[bt * N + m]; });
+      } else {
+        stage_columns(f0, nb);
+        cp_async_wait_all();
+        fft_batch<T, N, PE, -1, NT, N>(buf, nb, tw, stab);
+      }
       for (int j = tid; j < NK; j += NT) {
         const int ky = ky_of(j);
         const int idx = ky & (N - 1);
