@@ -366,12 +366,13 @@ def test_every_step_variant_matches_oracle(T, prec, n, dx, R):
     assert plan["n_row_variants"] >= 1 and plan["n_col_variants"] >= 1
     for rv in range(plan["n_row_variants"]):
         for cv in range(plan["n_col_variants"]):
-            dom.set_plan(rv, cv)
-            dom.set_spectral_state(w0, v00)
-            dom.step(steps)
-            vx, vy, w = dom.fields()
-            assert rel(w, O.vorticity(ref)) <= TOL[prec], (rv, cv)
-            assert rel(np.stack([vx, vy]), np.stack([ref.vx, ref.vy])) <= TOL[prec], (rv, cv)
+            for mode in (0, 3):   # ordinary launches with cp.async staging; PDL with TMA staging
+                dom.set_plan(rv, cv, launch_mode=mode)
+                dom.set_spectral_state(w0, v00)
+                dom.step(steps)
+                vx, vy, w = dom.fields()
+                assert rel(w, O.vorticity(ref)) <= TOL[prec], (rv, cv, mode)
+                assert rel(np.stack([vx, vy]), np.stack([ref.vx, ref.vy])) <= TOL[prec], (rv, cv, mode)
 
 
 def test_autotune_selects_a_valid_plan_and_keeps_state(T):
