@@ -25,7 +25,9 @@
  *    message for the last failure is returned by ttsh_last_error().
  *  - Kernels run on the domain's stream.  ttsh_step is asynchronous; calls that return
  *    host data synchronise the stream first.  A device-side failure surfaces as
- *    TTSH_E_CUDA at the next synchronising call.
+ *    TTSH_E_CUDA at the next synchronising call.  Every wait inside a kernel (TMA and
+ *    bulk-copy completion, tensor-core completion) is bounded; one that runs out sets a
+ *    status word that ttsh_synchronize / ttsh_diagnostics report as TTSH_E_TIMEOUT.
  */
 #ifndef TTSH_H
 #define TTSH_H
@@ -42,7 +44,7 @@ typedef enum {
   TTSH_E_INVALID = 1,      /* bad argument (size, pointer, parameter value)              */
   TTSH_E_OOM = 2,          /* device allocation failed                                    */
   TTSH_E_CUDA = 3,         /* a CUDA runtime call or kernel failed                        */
-  TTSH_E_TIMEOUT = 4,      /* reserved: a bounded device wait ran out                     */
+  TTSH_E_TIMEOUT = 4,      /* a bounded wait inside a kernel ran out                      */
   TTSH_E_NONFINITE = 5,    /* the state holds NaN or Inf (reported by ttsh_diagnostics)   */
   TTSH_E_UNSUPPORTED = 6   /* a valid request this build does not implement              */
 } ttsh_status;
@@ -357,7 +359,9 @@ ttsh_status ttsh_fno_correct(ttsh_fno* f, ttsh_domain* d, float* scratch);
  * Synchronises. */
 ttsh_status ttsh_fno_rollout(ttsh_fno* f, ttsh_domain* d, int64_t nsteps, int32_t correct_every, float* scratch);
 
-/* Block the host until the domain's stream is idle; reports deferred CUDA errors. */
+/* Block the host until the domain's stream is idle; reports deferred CUDA errors, and
+ * TTSH_E_TIMEOUT (once) if a bounded wait inside a kernel ran out since the last report (the
+ * affected steps are not valid; ttsh_diagnostics reports it too). */
 ttsh_status ttsh_synchronize(ttsh_domain* d);
 
 /* Steps taken since the last set_velocity / set_spectral_state. */
