@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-lyap", action="store_true")
+    ap.add_argument("--plan", default=None, metavar="ROW,COL[,MODE]",
+                    help="float32 step-kernel variants and launch mode instead of the autotuner's choice")
     return ap.parse_args()
 
 
@@ -135,7 +137,8 @@ def csrc_hash():
 
 def plan_variant(kernel, plan):
     if kernel == "row_pass":
-        return [plan["rows_per_block"], plan["row_points_per_thread"]]
+        cl = plan.get("row_cluster", 1)
+        return [plan["rows_per_block"], plan["row_points_per_thread"]] + ([cl] if cl > 1 else [])
     return [plan["col_points_per_thread"]]
 
 
@@ -275,7 +278,12 @@ def run_ours(args, rank, world, local_rank):
     # ---- float32 (headline) ----
     dom = ttsh.Domain(mask, n, dx, precision=32, stream=stream.cuda_stream)
     dom.set_velocity(vx0, vy0)
-    plan32 = dom.autotune(iters=max(20, min(400, int(4e7 // (n * n)))))   # untimed
+    if args.plan:
+        pv = [int(x) for x in args.plan.split(",")]
+        dom.set_plan(pv[0], pv[1], pv[2] if len(pv) > 2 else 0)
+        plan32 = dom.plan()
+    else:
+        plan32 = dom.autotune(iters=max(20, min(400, int(4e7 // (n * n)))))   # untimed
     for _ in range(W):
         advance(dom, S)
     dom.synchronize()

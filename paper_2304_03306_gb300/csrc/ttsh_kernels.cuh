@@ -106,6 +106,9 @@ template <typename T, int N>
 __host__ __device__ constexpr int default_row_pe() { return sizeof(T) == 4 ? 16 : 8; }
 template <typename T, int N>
 __host__ __device__ constexpr int default_col_pe() { return sizeof(T) == 4 ? (N <= 1024 ? 8 : 16) : 8; }
+// blocks per cluster of the default step row pass (8192^2 float: one row per block, pairs)
+template <typename T, int N>
+__host__ __device__ constexpr int default_row_cluster() { return sizeof(T) == 4 && N >= 8192 ? 2 : 1; }
 
 // Stride between the row buffers of one block: R-strided accesses (prep writes, post reads)
 // land on distinct banks when consecutive rows are 32/R banks apart.
@@ -113,8 +116,11 @@ __host__ __device__ constexpr int row_stride(int LP, int R, int words) {
   return R == 1 ? LP : LP + ((((32 / R) / words) % (32 / words) - LP % (32 / words)) % (32 / words) + (32 / words)) % (32 / words);
 }
 
-// Row-pass geometry and shared-memory plan.
-template <typename T, int N, int KIND, int R, int PEV>
+// Row-pass geometry and shared-memory plan.  CL > 1: the step kernel runs as clusters of CL
+// blocks over CL * R consecutive rows; each block stages one CL-th of the stored columns for
+// all the cluster's rows (global segments of CL * R values instead of R), and the blocks
+// read from each other's shares through distributed shared memory.
+template <typename T, int N, int KIND, int R, int PEV, int CL = 1>
 struct RowGeo {
   static constexpr int L = N / 2, M = N / 4, H = M + 1;
   static constexpr int PE = cmin(PEV, L);
@@ -132,8 +138,11 @@ struct RowGeo {
   // every region starts on a 16-byte boundary (16-byte cp.async destinations)
   static constexpr int BUF_BYTES = align16(F * R * LPR * CB);
   // staged G tile: plane f at OFF_GIN + f * GPS ([mx][r] inside a plane); planes start on
-  // 128-byte boundaries, as tensor-memory-accelerator destinations must
-  static constexpr int GPS = align128(H * R * CB);
+  // 128-byte boundaries, as tensor-memory-accelerator destinations must.  With clusters a
+  // block stages HC columns (its share) of RS rows (the cluster's).
+  static constexpr int HC = (H + CL - 1) / CL;
+  static constexpr int RS = R * CL;
+  static constexpr int GPS = align128(HC * RS * CB);
   static constexpr int GIN_BYTES = NPL * GPS;
   static constexpr int KS_BYTES = KIND == ROW_STEP ? align16(R * N * (int)sizeof(T)) : 0;
   static constexpr int RED_BYTES = KIND == ROW_INV_DIAG ? kDiagQ * 1024 * 8 : 0;
@@ -156,12 +165,14 @@ struct RowGeo {
   static constexpr int SMEM = OFF_FWD + (SEPARATE ? BUF_BYTES : 0) + 128;
   // the G tile can come by TMA: one box of R rows x (N/4+1) columns per plane (at most 256
   // columns in a box; a row segment of R complex values a multiple of 16 bytes)
-  static constexpr bool TMA_OK = STAGE_G && H <= 256 && (R * CB) % 16 == 0;
+  static constexpr bool TMA_OK = CL == 1 && STAGE_G && H <= 256 && (R * CB) % 16 == 0;
   static constexpr int NT = cmax(64, cmin(1024, F * R * TT));
-  static constexpr int SEG = R * CB;                        // bytes per (plane, mx) segment
+  static constexpr int SEG = RS * CB;                       // bytes per (plane, mx) segment
   static constexpr int CHUNK = SEG % 16 == 0 ? 16 : 8;
   static constexpr bool VALID = SMEM + (KIND == ROW_STEP ? kRecSmem : 0) <= 227 * 1024 && N % R == 0 &&
-                                R <= N && TT <= 1024 && NT % TT == 0;
+                                R <= N && TT <= 1024 && NT % TT == 0 &&
+                                (CL == 1 || (CL == 2 && KIND == ROW_STEP && STAGE_G && (N / R) % CL == 0 &&
+                                             SEG % 16 == 0));
   static_assert(OFF_BUF % 16 == 0 && OFF_GIN % 128 == 0 && GPS % 128 == 0 && OFF_KS % 16 == 0 &&
                 OFF_RED % 16 == 0 && OFF_FWD % 16 == 0,
                 "row pass shared-memory regions must be 16-byte (G tile: 128-byte) aligned");
@@ -289,14 +300,59 @@ __device__ __forceinline__ void record_sample(const Args<T>& A) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Thread-block clusters: rank, barrier, distributed shared memory
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Every thread of every block of the cluster arrives; shared-memory writes before it are
+// visible to every block of the cluster after it (a hardware barrier, no polling).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// Address of the same shared-memory location in block `rank` of this cluster.
+__device__ __forceinline__ unsigned dsmem_addr(const void* p, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r) : "r"((unsigned)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ cplx<float> dsmem_ld(unsigned a, float) {
+  float x, y;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a) : "memory");
+  return mk<float>(x, y);
+}
+__device__ __forceinline__ cplx<double> dsmem_ld(unsigned a, double) {
+  double x, y;
+  asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(x), "=d"(y) : "r"(a) : "memory");
+  return mk<double>(x, y);
+}
+__device__ __forceinline__ void dsmem_st(unsigned a, cplx<float> v) {
+  asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void dsmem_st(unsigned a, cplx<double> v) {
+  asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
+}
+
+// ---------------------------------------------------------------------------------------
 // Row pass body (one block = rows [y0, y0 + R))
 // ---------------------------------------------------------------------------------------
+// With CL = 2 (clusters of two blocks over 2R consecutive rows) block c of a cluster stages
+// the stored columns [c HC, c HC + HC) of both blocks' rows (global segments of 2R values),
+// slot (j, s) of a plane holding column c HC + j of the cluster's row s (s < R: block 0's
+// rows, s >= R: block 1's).  The first inverse stage reads the other block's share through
+// distributed shared memory; the forward results go back the same way into the share that
+// owns their column, and each block writes its share for all 2R rows.  Three cluster
+// barriers: shares staged; every block past its inverse loads (the shares are then
+// overwritten); results in place.
 // tmapG: G as a 2D tensor [3 (N/4+1)][2N scalars] with a box of R rows x (N/4+1), a grid-
 // constant kernel parameter (used when A.tma is set; may be null otherwise).
-template <typename T, int N, int KIND, int R, int PEV>
+template <typename T, int N, int KIND, int R, int PEV, int CL = 1>
 __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned char* smem_raw,
                                          const CUtensorMap* tmapG) {
-  using Geo = RowGeo<T, N, KIND, R, PEV>;
+  using Geo = RowGeo<T, N, KIND, R, PEV, CL>;
   static_assert(Geo::VALID, "row pass tile does not fit");
   constexpr int L = Geo::L, M = Geo::M, H = Geo::H;
   constexpr int NT = Geo::NT, PE = Geo::PE, PS = Geo::PS, LP = Geo::LPR;
@@ -306,6 +362,11 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
   T* ks = reinterpret_cast<T*>(smem_raw + Geo::OFF_KS);
   const int y0 = blk * R;
   const int tid = threadIdx.x;
+  constexpr int GPC = Geo::GPS / Geo::CB;   // G-tile plane stride in complex values
+  const int crank = CL > 1 ? (int)cluster_rank() : 0;
+  const int yc = y0 - crank * R;            // first row of the cluster
+  const int cbase = crank * Geo::HC;        // first stored column of this block's share
+  const int ccnt = cmin(Geo::HC, H - cbase);
 
   // ---- stage: twiddles and the K rows (inputs no previous kernel writes), then, once the
   // previous kernel has finished, the G tile (R consecutive y of every stored column) ----
@@ -352,15 +413,17 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
       constexpr int CPS = Geo::SEG / Geo::CHUNK;   // chunks per (plane, mx) segment
 #pragma unroll
       for (int pl = 0; pl < Geo::NPL; ++pl) {
-        const char* gsrc = reinterpret_cast<const char*>(A.G + (size_t)pl * H * N + y0);
+        const char* gsrc = reinterpret_cast<const char*>(A.G + ((size_t)pl * H + cbase) * N + yc);
         char* gdst = reinterpret_cast<char*>(gin) + pl * Geo::GPS;
-        for (int i = tid; i < H * CPS; i += NT)   // i = kx * CPS + c: the plane is [mx][r]
+        for (int i = tid; i < ccnt * CPS; i += NT)   // i = j * CPS + c: the plane is [mx][r]
           cp_async<Geo::CHUNK>(gdst + i * Geo::CHUNK, gsrc + (size_t)(i / CPS) * N * Geo::CB + (i % CPS) * Geo::CHUNK);
       }
     }
   }
   cp_async_wait_all();   // tables and staged inputs
   __syncthreads();
+
+  if constexpr (CL > 1) cluster_sync();   // every block's share is staged and visible
 
   // ---- inverse row transforms (C2R through an L-point complex transform) ----
   // The twiddle pre-pass that turns the half spectrum X of a real row into the L-point
@@ -372,9 +435,21 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
       cplx<T> X = mk<T>(0, 0), Xm = mk<T>(0, 0);
       const int km = L - k;
       if constexpr (Geo::STAGE_G) {
-        const cplx<T>* src = gin + (size_t)f * (Geo::GPS / Geo::CB) + r;
-        if (k <= M) X = src[k * R];
-        if (km <= M) Xm = src[km * R];
+        if constexpr (CL == 1) {
+          const cplx<T>* src = gin + (size_t)f * GPC + r;
+          if (k <= M) X = src[k * R];
+          if (km <= M) Xm = src[km * R];
+        } else {
+          // column kk of this block's row r: slot (kk - o HC, c R + r) of the share of block
+          // o that owns it, read through distributed shared memory when o is the other block
+          auto get = [&](int kk) -> cplx<T> {
+            const int o = kk < Geo::HC ? 0 : 1;
+            const int idx = f * GPC + (kk - o * Geo::HC) * Geo::RS + crank * R + r;
+            return o == crank ? gin[idx] : dsmem_ld(dsmem_addr(gin + idx, (unsigned)o), T());
+          };
+          if (k <= M) X = get(k);
+          if (km <= M) Xm = get(km);
+        }
       } else {
         const cplx<T>* src = A.G + (size_t)f * H * N + (y0 + r);
         if (k <= M) X = src[(size_t)k * N];
@@ -487,6 +562,8 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
   // ---- forward row transforms (R2C), keep mx <= N/4 ----
   if constexpr (FF > 0) {
     if constexpr (!Geo::SEPARATE) fft_batch<T, L, PE, -1, NT, N, LP>(sm, FF * R, tw, stab);
+    // clusters: every block is past its inverse loads, so the shares can take the results
+    if constexpr (CL > 1) cluster_sync();
     for (int e = tid; e < FF * R * H; e += NT) {
       const int r = e % R;
       const int t = e / R;
@@ -499,7 +576,27 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
       const cplx<T> d = Zk - Zm;
       // X[k] = (Zk + Zm)/2 - (i/2) W^k (Zk - Zm)
       const cplx<T> X = (s - mul_i(cmul(tw.get(k), d))) * (T)0.5;
-      A.Rr[((size_t)f * H + k) * N + (y0 + r)] = X;
+      if constexpr (CL == 1) {
+        A.Rr[((size_t)f * H + k) * N + (y0 + r)] = X;
+      } else {
+        // into slot (column, this block's row) of the share that owns column k
+        const int o = k < Geo::HC ? 0 : 1;
+        const int idx = f * GPC + (k - o * Geo::HC) * Geo::RS + crank * R + r;
+        if (o == crank) gin[idx] = X;
+        else dsmem_st(dsmem_addr(gin + idx, (unsigned)o), X);
+      }
+    }
+    if constexpr (CL > 1) {
+      cluster_sync();   // every row's results of this block's share are in place
+      // write the share: per plane and column, the cluster's RS consecutive y in 16-byte pieces
+      constexpr int PPS = Geo::SEG / 16;
+      for (int i = tid; i < FF * ccnt * PPS; i += NT) {
+        const int f = i / (ccnt * PPS), rem = i - f * (ccnt * PPS);
+        const int j = rem / PPS, pz = rem - j * PPS;
+        const uint4 v = *reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(gin) + f * Geo::GPS +
+                                                        j * Geo::SEG + pz * 16);
+        *reinterpret_cast<uint4*>(reinterpret_cast<char*>(A.Rr + ((size_t)f * H + cbase + j) * N + yc) + pz * 16) = v;
+      }
     }
   }
 }
@@ -720,11 +817,11 @@ __device__ __forceinline__ unsigned char* smem_base128(unsigned char* raw) {
 
 // The tensor map is a separate grid-constant parameter so that its address can be handed to
 // the TMA while the argument block stays an ordinary by-value parameter.
-template <typename T, int N, int KIND, int R, int PEV>
-__global__ void __launch_bounds__(RowGeo<T, N, KIND, R, PEV>::NT)
+template <typename T, int N, int KIND, int R, int PEV, int CL = 1>
+__global__ void __launch_bounds__(RowGeo<T, N, KIND, R, PEV, CL>::NT)
 row_kernel(Args<T> A, const __grid_constant__ CUtensorMap tmapG) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  row_body<T, N, KIND, R, PEV>(A, blockIdx.x, smem_base128(smem_raw), &tmapG);
+  row_body<T, N, KIND, R, PEV, CL>(A, blockIdx.x, smem_base128(smem_raw), &tmapG);
 }
 
 template <typename T, int N, int MODE, int PEV>

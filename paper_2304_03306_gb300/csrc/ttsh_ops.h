@@ -57,6 +57,7 @@ struct StepVariant {
   PrepareFn prepare;   // sets the batched kernel's attributes (call before graph capture)
   int rows;
   int pe;
+  int cl;   // blocks per cluster (row pass)
 };
 
 constexpr int kMaxBatchN = 1024;

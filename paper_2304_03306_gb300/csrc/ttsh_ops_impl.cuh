@@ -49,13 +49,13 @@ static cudaError_t set_smem(K kernel, int bytes, std::atomic<int>& done) {
   return e;
 }
 
-// Launch, optionally as a programmatic dependent launch: the kernel may start while the
+// Launch, optionally as a programmatic dependent launch (the kernel may start while the
 // previous kernel in the stream is still running; it waits (griddepcontrol.wait) before it
-// touches anything that kernel writes.
+// touches anything that kernel writes) and optionally in clusters of `cl` blocks along x.
 template <typename... P, typename... V>
 static cudaError_t launch_k(void (*kernel)(P...), int grid, int block, int smem, cudaStream_t s, bool pdl,
-                            const V&... args) {
-  if (!pdl) {
+                            int cl, const V&... args) {
+  if (!pdl && cl == 1) {
     kernel<<<grid, block, smem, s>>>(args...);
     return cudaGetLastError();
   }
@@ -64,19 +64,30 @@ static cudaError_t launch_k(void (*kernel)(P...), int grid, int block, int smem,
   cfg.blockDim = dim3(block);
   cfg.dynamicSmemBytes = (size_t)smem;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute at[2];
+  int na = 0;
+  if (pdl) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  if (cl > 1) {
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = (unsigned)cl;
+    at[na].val.clusterDim.y = 1;
+    at[na].val.clusterDim.z = 1;
+    ++na;
+  }
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = (unsigned)na;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <typename T, int N, int KIND, int R = default_rows<T, N>(), int PE = default_row_pe<T, N>()>
+template <typename T, int N, int KIND, int R = default_rows<T, N>(), int PE = default_row_pe<T, N>(), int CL = 1>
 static cudaError_t launch_row_kind(const DomainDev& d, cudaStream_t s) {
-  using Geo = RowGeo<T, N, KIND, R, PE>;
+  using Geo = RowGeo<T, N, KIND, R, PE, CL>;
   static std::atomic<int> done{0};
-  cudaError_t e = set_smem(row_kernel<T, N, KIND, R, PE>, Geo::SMEM, done);
+  cudaError_t e = set_smem(row_kernel<T, N, KIND, R, PE, CL>, Geo::SMEM, done);
   if (e != cudaSuccess) return e;
   Args<T> a = make_args<T>(d);
   CUtensorMap tm;
@@ -88,7 +99,8 @@ static cudaError_t launch_row_kind(const DomainDev& d, cudaStream_t s) {
       a.tma = 1;
     }
   }
-  return launch_k(row_kernel<T, N, KIND, R, PE>, N / R, Geo::NT, Geo::SMEM, s, KIND == ROW_STEP && d.pdl, a, tm);
+  return launch_k(row_kernel<T, N, KIND, R, PE, CL>, N / R, Geo::NT, Geo::SMEM, s, KIND == ROW_STEP && d.pdl, CL, a,
+                  tm);
 }
 
 template <typename T, int N, int MODE, int PE = default_col_pe<T, N>()>
@@ -99,7 +111,7 @@ static cudaError_t launch_col_mode(const DomainDev& d, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   // a recorded step adds one block that finishes the time-series sample
   const int extra = (MODE == COL_STEP && d.rec != nullptr) ? 1 : 0;
-  return launch_k(col_kernel<T, N, MODE, PE>, Geo::H + extra, Geo::NT, Geo::SMEM, s, MODE == COL_STEP && d.pdl,
+  return launch_k(col_kernel<T, N, MODE, PE>, Geo::H + extra, Geo::NT, Geo::SMEM, s, MODE == COL_STEP && d.pdl, 1,
                   make_args<T>(d));
 }
 
@@ -175,13 +187,15 @@ static void pack_args(const DomainDev& d, void* dst) {
   memcpy(dst, &a, sizeof(a));
 }
 
-template <typename T, int N, int R, int PE>
+template <typename T, int N, int R, int PE, int CL = 1>
 static void add_row_variant(SizeOps& o) {
-  if constexpr (RowGeo<T, N, ROW_STEP, R, PE>::VALID && (N >= 64 || (R == default_rows<T, N>() && PE == default_row_pe<T, N>()))) {
+  if constexpr (RowGeo<T, N, ROW_STEP, R, PE, CL>::VALID &&
+                (N >= 64 || (R == default_rows<T, N>() && PE == default_row_pe<T, N>() && CL == 1))) {
     for (int i = 0; i < o.n_row_variants; ++i)
-      if (o.row_step[i].rows == R && o.row_step[i].pe == cmin(PE, N / 2)) return;   // same shape
-    StepVariant v{&launch_row_kind<T, N, ROW_STEP, R, PE>, nullptr, nullptr, R, cmin(PE, N / 2)};
-    if constexpr (N <= kMaxBatchN) {
+      if (o.row_step[i].rows == R && o.row_step[i].pe == cmin(PE, N / 2) && o.row_step[i].cl == CL)
+        return;   // same shape
+    StepVariant v{&launch_row_kind<T, N, ROW_STEP, R, PE, CL>, nullptr, nullptr, R, cmin(PE, N / 2), CL};
+    if constexpr (N <= kMaxBatchN && CL == 1) {
       v.batched = &launch_row_batched<T, N, R, PE>;
       v.prepare = &prepare_row_batched<T, N, R, PE>;
     }
@@ -194,7 +208,7 @@ static void add_col_variant(SizeOps& o) {
   if constexpr (ColGeo<T, N, COL_STEP, PE>::VALID && (N >= 64 || PE == default_col_pe<T, N>())) {
     for (int i = 0; i < o.n_col_variants; ++i)
       if (o.col_step[i].pe == cmin(PE, N)) return;
-    StepVariant v{&launch_col_mode<T, N, COL_STEP, PE>, nullptr, nullptr, 1, cmin(PE, N)};
+    StepVariant v{&launch_col_mode<T, N, COL_STEP, PE>, nullptr, nullptr, 1, cmin(PE, N), 1};
     if constexpr (N <= kMaxBatchN) {
       v.batched = &launch_col_batched<T, N, PE>;
       v.prepare = &prepare_col_batched<T, N, PE>;
@@ -214,13 +228,18 @@ static SizeOps make_ops() {
   o.n_col_variants = 0;
   o.args_bytes = (int)sizeof(Args<T>);
   o.pack_args = &pack_args<T>;
-  add_row_variant<T, N, default_rows<T, N>(), default_row_pe<T, N>()>(o);
+  add_row_variant<T, N, default_rows<T, N>(), default_row_pe<T, N>(), default_row_cluster<T, N>()>(o);
   add_col_variant<T, N, default_col_pe<T, N>()>(o);
   if constexpr (sizeof(T) == 4) {
     add_row_variant<T, N, 4, 16>(o);
     add_row_variant<T, N, 2, 16>(o);
     add_row_variant<T, N, 1, 16>(o);
     add_row_variant<T, N, 2, 8>(o);
+    if constexpr (N >= 2048) {
+      // clusters of two blocks: global segments of 2R values (large grids, where R is small)
+      add_row_variant<T, N, 1, 16, 2>(o);
+      add_row_variant<T, N, 2, 16, 2>(o);
+    }
     add_col_variant<T, N, 8>(o);
     add_col_variant<T, N, 16>(o);
     add_col_variant<T, N, 4>(o);

@@ -242,7 +242,8 @@ def ttsh_time_kernels(h, iters: int):
 
 
 _PLAN_KEYS = ("row_variant", "col_variant", "rows_per_block", "row_points_per_thread",
-              "col_points_per_thread", "n_row_variants", "n_col_variants", "launch_mode")
+              "col_points_per_thread", "n_row_variants", "n_col_variants", "launch_mode",
+              "row_cluster")
 
 
 def _plan_dict(buf):
@@ -250,13 +251,13 @@ def _plan_dict(buf):
 
 
 def ttsh_autotune(h, iters: int = 200) -> dict:
-    buf = (ctypes.c_int32 * 8)()
+    buf = (ctypes.c_int32 * len(_PLAN_KEYS))()
     _check(load_library().ttsh_autotune(h, int(iters), buf))
     return _plan_dict(buf)
 
 
 def ttsh_get_plan(h) -> dict:
-    buf = (ctypes.c_int32 * 8)()
+    buf = (ctypes.c_int32 * len(_PLAN_KEYS))()
     _check(load_library().ttsh_get_plan(h, buf))
     return _plan_dict(buf)
 

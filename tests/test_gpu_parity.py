@@ -191,6 +191,68 @@ def test_linear_single_mode_closed_form(T, prec, n):
     assert rel(np.stack([gvx, gvy]), g * np.stack([vx, vy])) <= tol
 
 
+def _mode_fields(terms, X, Y):
+    """omega = sum a cos(kx x + ky y + ph) and its stream-function velocity
+    v = sum a / k^2 sin(kx x + ky y + ph) (-ky, kx), written analytically."""
+    w = np.zeros_like(X)
+    vx = np.zeros_like(X)
+    vy = np.zeros_like(X)
+    for a, kx, ky, ph in terms:
+        th = kx * X + ky * Y + ph
+        k2 = kx * kx + ky * ky
+        w += a * np.cos(th)
+        s = np.sin(th) * (a / k2)
+        vx -= ky * s
+        vy += kx * s
+    return vx, vy, w
+
+
+@pytest.mark.parametrize("n", [4096, 8192])
+def test_nonlinear_closed_forms_every_row_variant_at_full_size(T, n):
+    """One step of two closed forms with the nonlinear terms at work, at full grid sizes and
+    for every row-pass variant (clustered ones included): (i) b = 0, K = 0, omega =
+    A cos(px) + B cos(qy): the advection term makes the cos(px -+ qy) pair with amplitude
+    -+ dt lambda A B (p/q - q/p)/2; (ii) a single mode v = A e sin(theta), e perpendicular to
+    k: |v|^2 v = A^3 e (3/4 sin theta - 1/4 sin 3 theta), advection vanishes.  Every mode is
+    then multiplied by E(k) = exp[(a - (1 - k^2)^2) dt]."""
+    L = 16.0
+    dx = L / n
+    X, Y = ti.grid_coords(n, dx)
+    dk = 2 * np.pi / L
+    a_, dt, lam, b = 0.5, 0.01, 9.0, 1.6
+
+    def E(k2):
+        return np.exp((a_ - (1 - k2) ** 2) * dt)
+
+    p, q = 2 * dk, 3 * dk
+    A, B = 0.5, -0.8
+    c = -dt * lam * A * B * (p / q - q / p) / 2
+    adv0 = [(A, p, 0.0, 0.0), (B, 0.0, q, 0.0)]
+    adv1 = [(E(p * p) * A, p, 0.0, 0.0), (E(q * q) * B, 0.0, q, 0.0),
+            (c * E(p * p + q * q), p, -q, 0.0), (-c * E(p * p + q * q), p, q, 0.0)]
+    kx, ky, ph, Am = dk * 1, dk * 2, 0.4, 0.9
+    ka = np.hypot(kx, ky)
+    cub0 = [(Am * ka, kx, ky, ph)]
+    cub1 = [(E(ka * ka) * (Am * ka - dt * b * Am ** 3 * ka * 0.75), kx, ky, ph),
+            (E(9 * ka * ka) * (dt * b * Am ** 3 * ka * 0.75), 3 * kx, 3 * ky, 3 * ph)]
+    mask = np.zeros((n, n), np.uint8)
+    for bb, t0, t1 in ((0.0, adv0, adv1), (b, cub0, cub1)):
+        dom = T.Domain(mask, n, dx, precision=32, b=bb, lam=lam)
+        vx, vy, _ = _mode_fields(t0, X, Y)
+        dom.set_velocity(vx, vy)
+        w0, v00 = dom.spectral_state()
+        ex = _mode_fields(t1, X, Y)
+        plan = dom.plan()
+        for rv in range(plan["n_row_variants"]):
+            dom.set_plan(rv, 0, launch_mode=0)
+            dom.set_spectral_state(w0, v00)
+            dom.step(1)
+            gvx, gvy, gw = dom.fields()
+            assert rel(gw, ex[2]) <= 2e-5, (rv, dom.plan())
+            assert rel(np.stack([gvx, gvy]), np.stack(ex[:2])) <= 2e-5, (rv, dom.plan())
+        dom.close()
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_uniform_mask_closed_form(T, prec):
     """K_naive = 1 everywhere gives K = 1; with b = lambda = 0 each mode is multiplied by
