@@ -277,8 +277,10 @@ void ttsh_lyap_destroy(ttsh_lyap* L);
  *            otherwise); they must outlive the batch and are not copied.  The plan each
  *            domain has at creation is used; later ttsh_set_plan calls do not affect it.
  *   stream   stream the batch is issued on (NULL = legacy default).
- * ttsh_batch_step advances every domain by nsteps (asynchronous; it first waits for each
- * domain's own stream to be idle) and adds nsteps to their step counters. */
+ * ttsh_batch_step advances every domain by nsteps and adds nsteps to their step counters.
+ * It is asynchronous: work already queued on each domain's own stream is ordered before it by
+ * a device-side wait (the host does not block); whole multiples of 32 steps replay one graph,
+ * and a remainder replays a graph cached for the next call with the same remainder. */
 ttsh_status ttsh_batch_create(ttsh_domain* const* domains, int32_t ndom, void* stream, ttsh_batch** out);
 ttsh_status ttsh_batch_step(ttsh_batch* b, int64_t nsteps);
 ttsh_status ttsh_batch_synchronize(ttsh_batch* b);

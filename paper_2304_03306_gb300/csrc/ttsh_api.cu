@@ -435,6 +435,7 @@ int domain_add_vorticity_from_staging(ttsh_domain* d) {
 }
 double domain_dt(const ttsh_domain* d) { return d->p.dt; }
 int domain_refresh(ttsh_domain* d) { return run_col(d, K_COL_PROLOGUE, d->stream); }
+int domain_refresh_on(ttsh_domain* d, cudaStream_t s) { return run_col(d, K_COL_PROLOGUE, s); }
 
 // A second domain with the same parameters, processed mask, twiddles, plan, launch mode,
 // stream and state as src (device-to-device copies; the library allocates its workspace).
@@ -648,8 +649,11 @@ struct ttsh_batch {
   cudaStream_t stream = nullptr;
   cudaStream_t capture = nullptr;
   cudaEvent_t fork = nullptr;
-  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t order = nullptr;       // orders each domain's own stream before the batch's work
+  cudaGraphExec_t graph = nullptr;   // kBatchGraphLen steps
   int graph_len = 0;
+  cudaGraphExec_t tail = nullptr;    // the last call's remainder (tail_len < kBatchGraphLen steps)
+  int tail_len = 0;
 };
 
 namespace {
@@ -666,14 +670,15 @@ ttsh_status batch_group_steps(BatchGroup& g, int nsteps, cudaStream_t s) {
   return TTSH_OK;
 }
 
-ttsh_status batch_build_graph(ttsh_batch* b) {
+// Graph of `len` steps of every group, the groups as parallel branches.
+ttsh_status batch_build_graph(ttsh_batch* b, int len, cudaGraphExec_t* out) {
   TTSH_CUDA(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal), "begin capture");
   ttsh_status st = TTSH_OK;
   cudaError_t e = cudaEventRecord(b->fork, b->capture);
   for (size_t i = 0; i < b->groups.size() && e == cudaSuccess && st == TTSH_OK; ++i) {
     BatchGroup& g = b->groups[i];
     e = cudaStreamWaitEvent(g.branch, b->fork, 0);
-    if (e == cudaSuccess) st = batch_group_steps(g, kBatchGraphLen, g.branch);
+    if (e == cudaSuccess) st = batch_group_steps(g, len, g.branch);
     if (e == cudaSuccess && st == TTSH_OK) e = cudaEventRecord(g.join, g.branch);
     if (e == cudaSuccess && st == TTSH_OK) e = cudaStreamWaitEvent(b->capture, g.join, 0);
   }
@@ -684,13 +689,12 @@ ttsh_status batch_build_graph(ttsh_batch* b) {
     if (st != TTSH_OK) return st;
     return cuda_fail(e != cudaSuccess ? e : e2, "batch capture");
   }
-  e = cudaGraphInstantiate(&b->graph, graph, 0);
+  e = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {
-    b->graph = nullptr;
+    *out = nullptr;
     return cuda_fail(e, "batch graph instantiate");
   }
-  b->graph_len = kBatchGraphLen;
   return TTSH_OK;
 }
 
@@ -1273,6 +1277,7 @@ ttsh_status ttsh_batch_create(ttsh_domain* const* domains, int32_t ndom, void* s
   }
   cudaError_t e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->order, cudaEventDisableTiming);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "batch streams"));
   for (auto& g : b->groups) {
     const int ab = g.doms[0]->ops.args_bytes;
@@ -1293,18 +1298,35 @@ ttsh_status ttsh_batch_create(ttsh_domain* const* domains, int32_t ndom, void* s
 ttsh_status ttsh_batch_step(ttsh_batch* b, int64_t nsteps) {
   if (!b) return fail(TTSH_E_INVALID, "batch is NULL");
   if (nsteps < 0) return fail(TTSH_E_INVALID, "nsteps must be >= 0");
-  // every domain's own stream must be idle before the batch writes its state
-  for (ttsh_domain* d : b->all) TTSH_CUDA(cudaStreamSynchronize(d->stream), "domain stream");
+  // work already queued on a domain's own stream comes first (a device-side wait; the host
+  // does not block)
+  for (ttsh_domain* d : b->all) {
+    if (d->stream == b->stream) continue;
+    TTSH_CUDA(cudaEventRecord(b->order, d->stream), "order event");
+    TTSH_CUDA(cudaStreamWaitEvent(b->stream, b->order, 0), "order wait");
+  }
   ttsh_status st;
   int64_t left = nsteps;
-  if (left >= kBatchGraphLen && !b->graph)
-    if ((st = batch_build_graph(b)) != TTSH_OK) return st;
+  if (left >= kBatchGraphLen && !b->graph) {
+    if ((st = batch_build_graph(b, kBatchGraphLen, &b->graph)) != TTSH_OK) return st;
+    b->graph_len = kBatchGraphLen;
+  }
   while (b->graph && left >= b->graph_len) {
     TTSH_CUDA(cudaGraphLaunch(b->graph, b->stream), "batch graph launch");
     left -= b->graph_len;
   }
-  for (auto& g : b->groups)
-    if ((st = batch_group_steps(g, (int)left, b->stream)) != TTSH_OK) return st;
+  if (left > 0) {
+    // the remainder as a graph too (cached for the next call with the same remainder, such as
+    // a fixed renormalisation interval)
+    if (b->tail_len != (int)left) {
+      if (b->tail) cudaGraphExecDestroy(b->tail);
+      b->tail = nullptr;
+      b->tail_len = 0;
+      if ((st = batch_build_graph(b, (int)left, &b->tail)) != TTSH_OK) return st;
+      b->tail_len = (int)left;
+    }
+    TTSH_CUDA(cudaGraphLaunch(b->tail, b->stream), "batch graph launch");
+  }
   for (ttsh_domain* d : b->all) d->steps += nsteps;
   return TTSH_OK;
 }
@@ -1320,12 +1342,14 @@ int32_t ttsh_batch_groups(const ttsh_batch* b) { return b ? (int32_t)b->groups.s
 void ttsh_batch_destroy(ttsh_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->tail) cudaGraphExecDestroy(b->tail);
   for (auto& g : b->groups) {
     if (g.args_dev) cudaFree(g.args_dev);
     if (g.branch) cudaStreamDestroy(g.branch);
     if (g.join) cudaEventDestroy(g.join);
   }
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->order) cudaEventDestroy(b->order);
   if (b->capture) cudaStreamDestroy(b->capture);
   delete b;
 }

@@ -149,6 +149,8 @@ struct ttsh_lyap {
   void** ptrs = nullptr;     // [2][k + 1]: what pointers, vmean pointers
   long long steps = 0, intervals = 0;
   int interval = 0;
+  cudaStream_t cap = nullptr;          // private stream the renormalisation graph is captured on
+  cudaGraphExec_t renorm = nullptr;    // differences + CGS2 + reset of the copies, replayed per interval
 };
 
 namespace {
@@ -173,10 +175,9 @@ int grid_for(long long D) {
 }
 
 // Orthonormalise the k rows of L->Dl into L->Q (CGS2); with accumulate, record log R_ii.
-ttsh_status orthonormalise(ttsh_lyap* L, bool accumulate) {
+ttsh_status orthonormalise(ttsh_lyap* L, bool accumulate, cudaStream_t s) {
   using namespace lyap_dev;
   const int nb = grid_for(L->D);
-  cudaStream_t s = L->stream;
   for (int i = 0; i < L->k; ++i) {
     double* v = L->Dl + (size_t)i * L->D;
     if (i > 0) {
@@ -196,37 +197,65 @@ ttsh_status orthonormalise(ttsh_lyap* L, bool accumulate) {
 }
 
 // Reset every copy to base + eps Q_i and rebuild its inter-pass buffers.
-ttsh_status reset_copies(ttsh_lyap* L) {
+ttsh_status reset_copies(ttsh_lyap* L, cudaStream_t s) {
   dim3 g(grid_for(L->D), L->k);
   void** w = L->ptrs;
   void** m = L->ptrs + (L->k + 1);
   if (L->precision == 32)
-    lyap_dev::set_kernel<float><<<g, lyap_dev::kThreads, 0, L->stream>>>(
+    lyap_dev::set_kernel<float><<<g, lyap_dev::kThreads, 0, s>>>(
         reinterpret_cast<float* const*>(w), reinterpret_cast<float* const*>(m), L->Q, L->D, L->eps);
   else
-    lyap_dev::set_kernel<double><<<g, lyap_dev::kThreads, 0, L->stream>>>(
+    lyap_dev::set_kernel<double><<<g, lyap_dev::kThreads, 0, s>>>(
         reinterpret_cast<double* const*>(w), reinterpret_cast<double* const*>(m), L->Q, L->D, L->eps);
   LY_CUDA(cudaGetLastError(), "perturbation reset launch");
   for (ttsh_domain* p : L->perts) {
-    const int st = ttsh::domain_refresh(p);
+    const int st = ttsh::domain_refresh_on(p, s);
     if (st != TTSH_OK) return (ttsh_status)st;
   }
   return TTSH_OK;
 }
 
-ttsh_status differences(ttsh_lyap* L) {
+ttsh_status differences(ttsh_lyap* L, cudaStream_t s) {
   dim3 g(grid_for(L->D), L->k);
   void** w = L->ptrs;
   void** m = L->ptrs + (L->k + 1);
   if (L->precision == 32)
-    lyap_dev::diff_kernel<float><<<g, lyap_dev::kThreads, 0, L->stream>>>(
+    lyap_dev::diff_kernel<float><<<g, lyap_dev::kThreads, 0, s>>>(
         reinterpret_cast<const float* const*>(w), reinterpret_cast<const float* const*>(m), L->k, L->D,
         1.0 / L->eps, L->Dl);
   else
-    lyap_dev::diff_kernel<double><<<g, lyap_dev::kThreads, 0, L->stream>>>(
+    lyap_dev::diff_kernel<double><<<g, lyap_dev::kThreads, 0, s>>>(
         reinterpret_cast<const double* const*>(w), reinterpret_cast<const double* const*>(m), L->k, L->D,
         1.0 / L->eps, L->Dl);
   LY_CUDA(cudaGetLastError(), "difference launch");
+  return TTSH_OK;
+}
+
+// The end-of-interval work (differences, CGS2 with accumulation, reset of the copies) is the
+// same launch sequence with the same arguments every interval: capture it once on a private
+// stream and replay it on the domains' stream.
+ttsh_status renormalise(ttsh_lyap* L) {
+  if (!L->renorm) {
+    if (!L->cap) LY_CUDA(cudaStreamCreateWithFlags(&L->cap, cudaStreamNonBlocking), "capture stream");
+    LY_CUDA(cudaStreamBeginCapture(L->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    ttsh_status st = differences(L, L->cap);
+    if (st == TTSH_OK) st = orthonormalise(L, true, L->cap);
+    if (st == TTSH_OK) st = reset_copies(L, L->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(L->cap, &g);
+    if (st != TTSH_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (st != TTSH_OK) return st;
+      LY_CUDA(e, "renormalisation capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&L->renorm, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      L->renorm = nullptr;
+      LY_CUDA(ei, "renormalisation graph");
+    }
+  }
+  LY_CUDA(cudaGraphLaunch(L->renorm, L->stream), "renormalisation replay");
   return TTSH_OK;
 }
 
@@ -236,6 +265,8 @@ extern "C" {
 
 void ttsh_lyap_destroy(ttsh_lyap* L) {
   if (!L) return;
+  if (L->renorm) cudaGraphExecDestroy(L->renorm);
+  if (L->cap) cudaStreamDestroy(L->cap);
   if (L->batch) ttsh_batch_destroy(L->batch);
   for (ttsh_domain* p : L->perts) ttsh_destroy_domain(p);
   for (void* q : {(void*)L->Q, (void*)L->Dl, (void*)L->partial, (void*)L->coef, (void*)L->logs, (void*)L->last,
@@ -300,8 +331,8 @@ ttsh_status ttsh_lyap_create(ttsh_domain* base, int32_t k, double eps, const dou
     ttsh::set_last_error("Lyapunov set-up copies", e);
     return cleanup(TTSH_E_CUDA);
   }
-  ttsh_status st = orthonormalise(L, false);
-  if (st == TTSH_OK) st = reset_copies(L);
+  ttsh_status st = orthonormalise(L, false, s);
+  if (st == TTSH_OK) st = reset_copies(L, s);
   if (st != TTSH_OK) return cleanup(st);
   // batched stepping of the base and its copies where the grid allows it
   std::vector<ttsh_domain*> all{base};
@@ -337,9 +368,7 @@ ttsh_status ttsh_lyap_step(ttsh_lyap* L, int64_t nsteps, int32_t interval) {
       for (ttsh_domain* p : L->perts)
         if ((st = ttsh_step(p, interval)) != TTSH_OK) return st;
     }
-    if ((st = differences(L)) != TTSH_OK) return st;
-    if ((st = orthonormalise(L, true)) != TTSH_OK) return st;
-    if ((st = reset_copies(L)) != TTSH_OK) return st;
+    if ((st = renormalise(L)) != TTSH_OK) return st;
     L->steps += interval;
     L->intervals += 1;
   }

@@ -107,6 +107,7 @@ void domain_add_steps(ttsh_domain* d, int64_t n);
 double domain_dt(const ttsh_domain* d);
 // Rebuild the inter-pass buffers from the spectral state (after writing it on the device).
 int domain_refresh(ttsh_domain* d);
+int domain_refresh_on(ttsh_domain* d, cudaStream_t s);   // on another stream (graph capture)
 // Copy of a domain (parameters, mask, plan, stream, state) in a new library-owned workspace.
 int domain_clone(const ttsh_domain* src, ttsh_domain** out);
 
