@@ -122,7 +122,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("ttsh_fft.cuh", "ttsh_kernels.cuh", "ttsh_ops_impl.cuh")
+KERNEL_SOURCES = ("ttsh_fft.cuh", "ttsh_wait.cuh", "ttsh_kernels.cuh", "ttsh_ops_impl.cuh")
 
 
 def csrc_hash():

@@ -364,6 +364,14 @@ ttsh_status ttsh_fno_correct(ttsh_fno* f, ttsh_domain* d, float* scratch);
  * Synchronises. */
 ttsh_status ttsh_fno_rollout(ttsh_fno* f, ttsh_domain* d, int64_t nsteps, int32_t correct_every, float* scratch);
 
+/* Test hook of the failure path (no counterpart in the paper): launches, on the domain's
+ * stream, one block whose bounded wait is on an mbarrier phase that nothing completes, limited
+ * to `seconds` (0 < seconds <= 1, else TTSH_E_INVALID).  The wait runs out and sets the
+ * domain's status word exactly as a lost TMA, bulk-copy or tensor-core completion would, so
+ * the next ttsh_synchronize returns TTSH_E_TIMEOUT once; the CUDA context and the domain
+ * stay usable.  (Production waits are limited to 2 s.) */
+ttsh_status ttsh_test_bounded_wait(ttsh_domain* d, double seconds);
+
 /* Block the host until the domain's stream is idle; reports deferred CUDA errors, and
  * TTSH_E_TIMEOUT (once) if a bounded wait inside a kernel ran out since the last report (the
  * affected steps are not valid; ttsh_diagnostics reports it too). */

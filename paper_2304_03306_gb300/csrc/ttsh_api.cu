@@ -16,9 +16,19 @@
 #include <unordered_set>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>   // header-only: ranges are free unless a profiler attaches
+
 #include "ttsh.h"
 #include "ttsh_kernels.cuh"
 #include "ttsh_ops.h"
+
+// Host-side NVTX range over one API call (visible to ncu --nvtx / Nsight timelines).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 namespace {
 
@@ -187,6 +197,18 @@ struct ttsh_domain {
   int rec_len = 0, rec_every = 0, rec_rv = -1, rec_cv = -1;
   double rec_cx = 0.0, rec_cy = 0.0;
 };
+
+namespace ttsh {
+// Test hook of the failure path: one block waits on an mbarrier phase that nothing completes
+// (no arrival is ever made), bounded by limit_ns; the wait runs out and sets the status word.
+__global__ void expire_wait_kernel(int* err, unsigned long long limit_ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait_bounded(a, 0, limit_ns)) atomicExch(err, 1);
+}
+}  // namespace ttsh
 
 namespace {
 
@@ -924,6 +946,7 @@ ttsh_status ttsh_set_velocity_device(ttsh_domain* d, const double* vx, const dou
 }
 
 ttsh_status ttsh_step(ttsh_domain* d, int64_t nsteps) {
+  NvtxRange nvtx_range("ttsh_step");
   if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
   if (nsteps < 0) return fail(TTSH_E_INVALID, "nsteps must be >= 0");
   ttsh_status st;
@@ -951,6 +974,7 @@ ttsh_status ttsh_step(ttsh_domain* d, int64_t nsteps) {
 
 ttsh_status ttsh_step_record(ttsh_domain* d, int64_t nsteps, int32_t every, double* series,
                              int64_t capacity, const double* centre) {
+  NvtxRange nvtx_range("ttsh_step_record");
   if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
   if (nsteps < 0) return fail(TTSH_E_INVALID, "nsteps must be >= 0");
   if (every < 1) return fail(TTSH_E_INVALID, "every must be >= 1");
@@ -1086,6 +1110,7 @@ ttsh_status ttsh_set_spectral_state(ttsh_domain* d, const double* w_hat, const d
 
 ttsh_status ttsh_diagnostics(ttsh_domain* d, ttsh_diag* out, double* spectrum, int32_t nbins,
                              const double* centre) {
+  NvtxRange nvtx_range("ttsh_diagnostics");
   if (!d || !out) return fail(TTSH_E_INVALID, "NULL argument");
   if (nbins < 0 || nbins > 65536) return fail(TTSH_E_INVALID, "nbins must be in [0, 65536]");
   if (nbins > 0 && !spectrum) return fail(TTSH_E_INVALID, "spectrum is NULL");
@@ -1147,6 +1172,7 @@ ttsh_status ttsh_time_kernels(ttsh_domain* d, int32_t iters, double* ms) {
 }
 
 ttsh_status ttsh_autotune(ttsh_domain* d, int32_t iters, int32_t* plan) {
+  NvtxRange nvtx_range("ttsh_autotune");
   if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
   if (iters < 1 || iters > 100000) return fail(TTSH_E_INVALID, "iters must be in [1, 100000]");
   ttsh_status st = save_state(d);
@@ -1296,6 +1322,7 @@ ttsh_status ttsh_batch_create(ttsh_domain* const* domains, int32_t ndom, void* s
 }
 
 ttsh_status ttsh_batch_step(ttsh_batch* b, int64_t nsteps) {
+  NvtxRange nvtx_range("ttsh_batch_step");
   if (!b) return fail(TTSH_E_INVALID, "batch is NULL");
   if (nsteps < 0) return fail(TTSH_E_INVALID, "nsteps must be >= 0");
   // work already queued on a domain's own stream comes first (a device-side wait; the host
@@ -1458,6 +1485,14 @@ ttsh_status ttsh_synchronize(ttsh_domain* d) {
   ttsh_status st = sync(d, "synchronize");
   if (st != TTSH_OK) return st;
   return check_status(d);
+}
+
+ttsh_status ttsh_test_bounded_wait(ttsh_domain* d, double seconds) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  if (!(seconds > 0.0) || seconds > 1.0) return fail(TTSH_E_INVALID, "seconds must be in (0, 1]");
+  ttsh::expire_wait_kernel<<<1, 32, 0, d->stream>>>(d->dev.err, (unsigned long long)(seconds * 1e9));
+  TTSH_CUDA(cudaGetLastError(), "bounded-wait test launch");
+  return TTSH_OK;
 }
 
 int64_t ttsh_step_count(const ttsh_domain* d) { return d ? d->steps : -1; }

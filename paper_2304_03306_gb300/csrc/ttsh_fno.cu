@@ -24,6 +24,7 @@
 
 #include "ttsh.h"
 #include "ttsh_ops.h"
+#include "ttsh_wait.cuh"
 
 namespace fno_dev {
 
@@ -165,7 +166,6 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
 }
 
 constexpr int kTcRows = 128;
-constexpr long long kTcSpin = 1ll << 24;   // bound on the completion wait (polls)
 
 // (r, k) of a 128 x 32 (or 32 x 32) BF16 K-major tile -> byte offset in the core-matrix layout
 __device__ __forceinline__ int core_off(int r, int kc) { return (r >> 3) * 512 + kc * 128 + (r & 7) * 16; }
@@ -221,10 +221,7 @@ __global__ void __launch_bounds__(128) pointwise_tc_kernel(PwArgs a) {
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    ::"r"(smem_u32(&mbar)) : "memory");
     }
-    uint32_t done = 0;
-    for (long long it = 0; it < kTcSpin && !done; ++it)
-      asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                   : "=r"(done) : "r"(smem_u32(&mbar)), "r"(phase) : "memory");
+    const bool done = ttsh::mbar_wait_bounded(smem_u32(&mbar), phase, ttsh::kWaitLimitNs);
     if (__syncthreads_or(!done)) {
       if (tid == 0) atomicExch(a.err, 1);
       break;

@@ -39,6 +39,7 @@
 #include <cuda.h>   // CUtensorMap (the tensor-map descriptor of the TMA loads)
 
 #include "ttsh_fft.cuh"
+#include "ttsh_wait.cuh"
 
 namespace ttsh {
 
@@ -84,7 +85,6 @@ enum ColMode { COL_STEP = 0, COL_PROLOGUE = 1, COL_PROJECT = 2, COL_MASK = 3, CO
 constexpr int kDiagQ = 5;   // per-block partials: sum|v|^2, sum w^2, sum|e_th.v|, sum|v|, #nonfinite
 constexpr int kSmemLimit = 220 * 1024;
 constexpr int kRecSmem = 32 * kDiagQ * 8 + 16;   // static shared memory: time-series reduction, TMA barrier
-constexpr long long kTmaSpin = 1ll << 24;        // bound on the TMA completion wait (polls)
 
 __host__ __device__ constexpr int align16(int v) { return (v + 15) / 16 * 16; }
 __host__ __device__ constexpr int align128(int v) { return (v + 127) / 128 * 128; }
@@ -404,11 +404,7 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
               ::"r"(dst), "l"(tmapG), "r"(x), "r"(y), "r"(bar) : "memory");
         }
       }
-      unsigned done = 0;
-      for (long long it = 0; it < kTmaSpin && !done; ++it)
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done) : "r"(bar) : "memory");
-      if (!done) atomicExch(A.err, 1);
+      if (!mbar_wait_bounded(bar, 0, kWaitLimitNs)) atomicExch(A.err, 1);
     } else {
       constexpr int CPS = Geo::SEG / Geo::CHUNK;   // chunks per (plane, mx) segment
 #pragma unroll
@@ -659,11 +655,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
                        : "memory");
         }
       }
-      unsigned done = 0;
-      for (long long it = 0; it < kTmaSpin && !done; ++it)
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(done) : "r"(bar) : "memory");
-      if (!done && A.err) atomicExch(A.err, 1);
+      if (!mbar_wait_bounded(bar, 0, kWaitLimitNs) && A.err) atomicExch(A.err, 1);
     }
     for (int f0 = 0; f0 < NF; f0 += FB) {
       const int nb = cmin(FB, NF - f0);

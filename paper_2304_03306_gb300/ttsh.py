@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH):
         "ttsh_set_spectral_state": (ctypes.c_int, [_P, _D, _D]),
         "ttsh_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(ttsh_diag), _D, ctypes.c_int32, _D]),
         "ttsh_synchronize": (ctypes.c_int, [_P]),
+        "ttsh_test_bounded_wait": (ctypes.c_int, [_P, ctypes.c_double]),
         "ttsh_time_kernels": (ctypes.c_int, [_P, ctypes.c_int32, _D]),
         "ttsh_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
         "ttsh_get_plan": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
@@ -493,6 +494,10 @@ class Domain:
 
     def synchronize(self):
         ttsh_synchronize(self.h)
+
+    def test_bounded_wait(self, seconds: float):
+        """Failure-path test hook: a kernel whose bounded wait cannot complete (see ttsh.h)."""
+        _check(load_library().ttsh_test_bounded_wait(self.h, float(seconds)))
 
     def autotune(self, iters: int = 200) -> dict:
         """Time every tile-shape variant of the step kernels and keep the fastest."""

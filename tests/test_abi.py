@@ -68,6 +68,7 @@ def test_null_arguments_are_rejected(lib):
     from paper_2304_03306_gb300 import ttsh
     assert lib.ttsh_step(None, 1) == ttsh.TTSH_E_INVALID
     assert lib.ttsh_synchronize(None) == ttsh.TTSH_E_INVALID
+    assert lib.ttsh_test_bounded_wait(None, ctypes.c_double(1e-3)) == ttsh.TTSH_E_INVALID
     assert "NULL" in ttsh.ttsh_last_error()
     assert lib.ttsh_step_count(None) == -1
     lib.ttsh_destroy_domain(None)   # no-op

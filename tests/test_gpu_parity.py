@@ -332,6 +332,25 @@ def test_nonfinite_state_is_reported(T):
     assert d["status"] == T.TTSH_E_NONFINITE and d["nonfinite"] > 0
 
 
+def test_bounded_wait_timeout_is_reported_once_and_the_domain_stays_usable(T):
+    """Failure detection without a GPU fault: a kernel's bounded wait on an mbarrier phase
+    that nothing completes runs out after 1 ms and sets the status word; ttsh_synchronize
+    reports TTSH_E_TIMEOUT once, and stepping afterwards still matches the oracle."""
+    n, dx = 64, 0.25
+    dom, p, K, s = setup(T, n, dx, 5.2, 32, 1, amp=0.3)
+    dom.step(5)
+    dom.synchronize()
+    with pytest.raises(T.TTSHError):
+        dom.test_bounded_wait(0.0)
+    dom.test_bounded_wait(1e-3)
+    with pytest.raises(T.TTSHError) as e:
+        dom.synchronize()
+    assert e.value.status == T.TTSH_E_TIMEOUT
+    dom.synchronize()   # reported once
+    dom.step(10)
+    check_fields(dom, O.run(s, K, p, 15), TOL[32])
+
+
 # ------------------------------------------------------- checkpoint / graphs
 
 @pytest.mark.parametrize("prec", [32, 64])
