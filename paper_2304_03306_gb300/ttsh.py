@@ -140,6 +140,13 @@ def _f64(a, n):
     return a
 
 
+def _centre(centre):
+    c = np.ascontiguousarray(centre, dtype=np.float64).reshape(-1)
+    if c.shape != (2,):
+        raise ValueError("centre must hold two coordinates")
+    return c
+
+
 def ttsh_last_error() -> str:
     return load_library().ttsh_last_error().decode()
 
@@ -191,7 +198,7 @@ def ttsh_step(h, nsteps: int):
 def ttsh_step_record(h, nsteps: int, every: int, series_ptr: int | None, capacity: int, centre=(0.0, 0.0)):
     """Step and append {step, energy, enstrophy, psi, nonfinite} every `every` steps to the
     device array at series_ptr (5 * capacity doubles).  Asynchronous."""
-    c = np.ascontiguousarray(centre, dtype=np.float64)
+    c = _centre(centre)
     _check(load_library().ttsh_step_record(h, int(nsteps), int(every), series_ptr, int(capacity), _dptr(c)))
 
 
@@ -215,16 +222,22 @@ def ttsh_get_spectral_state(h, n: int):
     return buf[..., 0] + 1j * buf[..., 1], v0
 
 
-def ttsh_set_spectral_state(h, w_hat, v0):
+def ttsh_set_spectral_state(h, w_hat, v0, n: int):
+    M = n // 4
+    w_hat = np.asarray(w_hat)
+    if w_hat.shape != (M + 1, 2 * M + 1):
+        raise ValueError(f"w_hat must have shape {(M + 1, 2 * M + 1)}, got {w_hat.shape}")
     buf = np.ascontiguousarray(np.stack([np.real(w_hat), np.imag(w_hat)], axis=-1), dtype=np.float64)
-    v = np.ascontiguousarray(v0, dtype=np.float64)
+    v = np.ascontiguousarray(v0, dtype=np.float64).reshape(-1)
+    if v.shape != (2,):
+        raise ValueError("v0 must hold the two mean-flow components")
     _check(load_library().ttsh_set_spectral_state(h, _dptr(buf), _dptr(v)))
 
 
 def ttsh_diagnostics(h, nbins: int = 0, centre=(0.0, 0.0)) -> dict:
     d = ttsh_diag()
     spec = np.zeros(max(nbins, 1))
-    c = np.ascontiguousarray(centre, dtype=np.float64)
+    c = _centre(centre)
     st = load_library().ttsh_diagnostics(h, ctypes.byref(d), _dptr(spec) if nbins else None,
                                          int(nbins), _dptr(c))
     if st not in (TTSH_OK, TTSH_E_NONFINITE):
@@ -487,7 +500,7 @@ class Domain:
         return ttsh_get_spectral_state(self.h, self.n)
 
     def set_spectral_state(self, w_hat, v0):
-        ttsh_set_spectral_state(self.h, w_hat, v0)
+        ttsh_set_spectral_state(self.h, w_hat, v0, self.n)
 
     def diagnostics(self, nbins: int = 0, centre=(0.0, 0.0)):
         return ttsh_diagnostics(self.h, nbins, centre)
@@ -540,7 +553,12 @@ class Lyapunov:
 
     def __init__(self, dom: "Domain", q0, eps: float):
         q0 = np.ascontiguousarray(q0, dtype=np.float64)
+        if q0.ndim != 2:
+            raise ValueError("q0 must be a (k, D) array of directions")
         self.k, self.D = q0.shape
+        D = 2 * (dom.n // 4 + 1) * (dom.n // 2 + 1) + 2
+        if self.D != D:
+            raise ValueError(f"each direction must have D = {D} entries for n = {dom.n}")
         self.h = _P()
         _check(load_library().ttsh_lyap_create(dom.h, self.k, float(eps), _dptr(q0), ctypes.byref(self.h)))
 

@@ -82,3 +82,22 @@ def test_product_path_has_no_oracle_import():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, re.M), f
                 assert "ttsh_oracle" not in text, f
+
+
+def test_binding_rejects_mis_shaped_arrays_before_the_call():
+    """Arrays whose size the library derives from the grid are checked in the binding, so a
+    wrong shape never reaches the C side (which would read past the end)."""
+    from paper_2304_03306_gb300 import ttsh
+    n = 64
+    M = n // 4
+    with pytest.raises(ValueError):
+        ttsh.ttsh_set_spectral_state(None, np.zeros((M, 2 * M + 1), complex), np.zeros(2), n)
+    with pytest.raises(ValueError):
+        ttsh.ttsh_set_spectral_state(None, np.zeros((M + 1, 2 * M + 1), complex), np.zeros(3), n)
+    with pytest.raises(ValueError):
+        ttsh.ttsh_step_record(None, 10, 1, None, 10, centre=(0.0,))
+
+    class FakeDomain:
+        n = 64
+    with pytest.raises(ValueError):
+        ttsh.Lyapunov(FakeDomain(), np.zeros((2, 100)), 1e-3)
