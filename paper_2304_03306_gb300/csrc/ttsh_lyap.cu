@@ -75,30 +75,53 @@ __global__ void dots_kernel(const double* __restrict__ v, const double* __restri
   }
 }
 
-// coef[j] = sum over blocks (in block order) of the partials of slot j.
-__global__ void reduce_kernel(const double* __restrict__ partial, int nblocks, int nd, double* __restrict__ coef) {
-  const int j = threadIdx.x;
-  if (j >= nd) return;
+// Slot j of the block partials summed over the nb blocks in block order (every consumer
+// block computes the same sum, so no separate reduction launch is needed).
+__device__ __forceinline__ double partial_sum(const double* __restrict__ partial, int nb, int j) {
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * (kMaxK + 1) + j];
-  coef[j] = s;
+  for (int b = 0; b < nb; ++b) s += partial[(size_t)b * (kMaxK + 1) + j];
+  return s;
 }
 
-// v -= sum_j coef[j] Q_j (j in order)
-__global__ void axpy_kernel(double* __restrict__ v, const double* __restrict__ Q, const double* __restrict__ coef,
-                            int nq, long long D) {
+// v -= sum_j c_j Q_j (j in order), c_j = <v, Q_j> from the partials of slots 0..nq-1.  With
+// norm, the block partial of <v, v> of the result goes to slot kMaxK (same summation order
+// as dots_kernel with self).
+__global__ void axpy_kernel(double* __restrict__ v, const double* __restrict__ Q, double* __restrict__ partial,
+                            int nb, int nq, long long D, long long col2, int norm) {
+  __shared__ double c[kMaxK];
+  __shared__ double red[kThreads];
+  if ((int)threadIdx.x < nq) c[threadIdx.x] = partial_sum(partial, nb, threadIdx.x);
+  __syncthreads();
+  double acc = 0.0;
   for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < D; x += (long long)gridDim.x * blockDim.x) {
     double s = v[x];
-    for (int j = 0; j < nq; ++j) s -= coef[j] * Q[(size_t)j * D + x];
+    for (int j = 0; j < nq; ++j) s -= c[j] * Q[(size_t)j * D + x];
     v[x] = s;
+    if (norm) {
+      const double wv = weight(x, col2, D) * s;
+      acc += wv * s;
+    }
+  }
+  if (norm) {
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int t = kThreads / 2; t >= 1; t >>= 1) {
+      if ((int)threadIdx.x < t) red[threadIdx.x] += red[threadIdx.x + t];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(size_t)blockIdx.x * (kMaxK + 1) + kMaxK] = red[0];
   }
 }
 
-// q = v / r with r = sqrt(coef[slot]); with accumulate, logs[i] += log r and last[i] = log r.
-__global__ void scale_kernel(const double* __restrict__ v, double* __restrict__ q, const double* __restrict__ coef,
-                             int slot, long long D, int i, int accumulate, double* __restrict__ logs,
+// q = v / r with r = sqrt(<v, v>) from the partials of `slot`; with accumulate,
+// logs[i] += log r and last[i] = log r.
+__global__ void scale_kernel(const double* __restrict__ v, double* __restrict__ q, const double* __restrict__ partial,
+                             int nb, int slot, long long D, int i, int accumulate, double* __restrict__ logs,
                              double* __restrict__ last) {
-  const double r = sqrt(coef[slot]);
+  __shared__ double r2;
+  if (threadIdx.x == 0) r2 = partial_sum(partial, nb, slot);
+  __syncthreads();
+  const double r = sqrt(r2);
   const double inv = 1.0 / r;
   for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < D; x += (long long)gridDim.x * blockDim.x)
     q[x] = v[x] * inv;
@@ -141,8 +164,7 @@ struct ttsh_lyap {
   double eps = 0.0, dt = 0.0;
   double* Q = nullptr;       // [k][D] orthonormal directions
   double* Dl = nullptr;      // [k][D] evolved perturbations
-  double* partial = nullptr; // [kBlocks][kMaxK + 1]
-  double* coef = nullptr;    // [kMaxK + 1]
+  double* partial = nullptr; // [kBlocks][kMaxK + 1]: dot-product partials; slot kMaxK: norms
   double* logs = nullptr;    // [k]
   double* last = nullptr;    // [k]
   double* out = nullptr;     // [2k]
@@ -178,19 +200,22 @@ int grid_for(long long D) {
 ttsh_status orthonormalise(ttsh_lyap* L, bool accumulate, cudaStream_t s) {
   using namespace lyap_dev;
   const int nb = grid_for(L->D);
+  // per vector: two projection passes (dots, then axpy reducing the dots' partials itself;
+  // the second axpy also forms the norm's partials), then the scaling
   for (int i = 0; i < L->k; ++i) {
     double* v = L->Dl + (size_t)i * L->D;
+    int slot = 0;
     if (i > 0) {
       for (int pass = 0; pass < 2; ++pass) {
         dots_kernel<<<nb, kThreads, 0, s>>>(v, L->Q, i, 0, L->D, L->col2, L->partial);
-        reduce_kernel<<<1, 32, 0, s>>>(L->partial, nb, i, L->coef);
-        axpy_kernel<<<nb, kThreads, 0, s>>>(v, L->Q, L->coef, i, L->D);
+        axpy_kernel<<<nb, kThreads, 0, s>>>(v, L->Q, L->partial, nb, i, L->D, L->col2, pass);
       }
+      slot = kMaxK;
+    } else {
+      dots_kernel<<<nb, kThreads, 0, s>>>(v, L->Q, 0, 1, L->D, L->col2, L->partial);
     }
-    dots_kernel<<<nb, kThreads, 0, s>>>(v, L->Q, 0, 1, L->D, L->col2, L->partial);
-    reduce_kernel<<<1, 32, 0, s>>>(L->partial, nb, 1, L->coef);
-    scale_kernel<<<nb, kThreads, 0, s>>>(v, L->Q + (size_t)i * L->D, L->coef, 0, L->D, i, accumulate ? 1 : 0,
-                                         L->logs, L->last);
+    scale_kernel<<<nb, kThreads, 0, s>>>(v, L->Q + (size_t)i * L->D, L->partial, nb, slot, L->D, i,
+                                         accumulate ? 1 : 0, L->logs, L->last);
   }
   LY_CUDA(cudaGetLastError(), "orthonormalisation launch");
   return TTSH_OK;
@@ -269,7 +294,7 @@ void ttsh_lyap_destroy(ttsh_lyap* L) {
   if (L->cap) cudaStreamDestroy(L->cap);
   if (L->batch) ttsh_batch_destroy(L->batch);
   for (ttsh_domain* p : L->perts) ttsh_destroy_domain(p);
-  for (void* q : {(void*)L->Q, (void*)L->Dl, (void*)L->partial, (void*)L->coef, (void*)L->logs, (void*)L->last,
+  for (void* q : {(void*)L->Q, (void*)L->Dl, (void*)L->partial, (void*)L->logs, (void*)L->last,
                   (void*)L->out, (void*)L->ptrs})
     if (q) cudaFree(q);
   delete L;
@@ -306,7 +331,6 @@ ttsh_status ttsh_lyap_create(ttsh_domain* base, int32_t k, double eps, const dou
   cudaError_t e = cudaMalloc(&L->Q, kd);
   if (e == cudaSuccess) e = cudaMalloc(&L->Dl, kd);
   if (e == cudaSuccess) e = cudaMalloc(&L->partial, (size_t)lyap_dev::kBlocks * (lyap_dev::kMaxK + 1) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&L->coef, (lyap_dev::kMaxK + 1) * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&L->logs, k * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&L->last, k * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&L->out, 2 * k * sizeof(double));
