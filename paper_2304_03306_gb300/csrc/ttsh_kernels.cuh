@@ -218,8 +218,8 @@ struct ColGeo {
 // Time-series sample taken inside a step's row pass.  The pass already holds omega, v_x and
 // v_y of its R rows in real space (the state the step starts from), so the energy,
 // enstrophy and order-parameter sums cost one extra sweep over shared memory: per-thread
-// sums in T over the thread's points, then a fixed-order reduction in double (shuffles
-// inside a warp, warps in index order) to kDiagQ partials per block, written to A.rec.
+// and per-warp sums in T (fixed-order shuffles), then the warps in index order in double,
+// to kDiagQ partials per block, written to A.rec.
 // Same quantities as ROW_INV_DIAG: sum |v|^2, sum omega^2, sum |e_theta . v| (e_theta = 0 at
 // the centre), sum |v|, number of points with a non-finite value.
 // ---------------------------------------------------------------------------------------
@@ -241,7 +241,9 @@ __device__ __forceinline__ void record_partials(const Args<T>& A, int blk, int y
     s3 += sqrt(v2);
     bad += (isfinite(w) && isfinite(vx) && isfinite(vy)) ? 0 : 1;
   }
-  double q[kDiagQ] = {(double)s0, (double)s1, (double)s2, (double)s3, (double)bad};
+  // warp sums in T (the per-thread sums already are; on GB300 a double add costs 16x a
+  // float one), then the warps' sums in double
+  T q[kDiagQ - 1] = {s0, s1, s2, s3};
   constexpr int NW = (NT + 31) / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int wl = cmin(32, NT - warp * 32);   // lanes present in this warp
@@ -249,14 +251,18 @@ __device__ __forceinline__ void record_partials(const Args<T>& A, int blk, int y
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-    for (int k = 0; k < kDiagQ; ++k) {
-      const double o = __shfl_down_sync(mask, q[k], off);
+    for (int k = 0; k < kDiagQ - 1; ++k) {
+      const T o = __shfl_down_sync(mask, q[k], off);
       if (lane + off < wl) q[k] += o;
     }
+    const int ob = __shfl_down_sync(mask, bad, off);
+    if (lane + off < wl) bad += ob;
   }
   __shared__ double wsum[NW][kDiagQ];
-  if (lane == 0)
-    for (int k = 0; k < kDiagQ; ++k) wsum[warp][k] = q[k];
+  if (lane == 0) {
+    for (int k = 0; k < kDiagQ - 1; ++k) wsum[warp][k] = (double)q[k];
+    wsum[warp][kDiagQ - 1] = (double)bad;
+  }
   __syncthreads();
   if (threadIdx.x < kDiagQ) {
     double t = 0.0;
