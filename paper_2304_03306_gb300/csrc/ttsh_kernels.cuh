@@ -207,8 +207,12 @@ struct ColGeo {
   static constexpr int OFF_STG = OFF_WS + WS_BYTES;
   static constexpr int OFF_S0 = OFF_STG + (BULK ? STG_BYTES : 0);
   static constexpr int SMEM = OFF_S0 + 64;
-  static constexpr int NT = cmax(64, cmin(1024, FB * TT));
-  static constexpr bool VALID = SMEM <= 227 * 1024 && TT <= 1024 && NT % TT == 0;
+  // transforms in flight at once: as many of the FB as fit in the thread budget; with 16
+  // points per thread the budget is 768 threads (85 registers each), since 1024 threads
+  // (64 registers) make the radix-16 butterflies spill
+  static constexpr int NTCAP = PE >= 16 ? 768 : 1024;
+  static constexpr int NT = cmax(64, TT * cmax(1, cmin(FB, NTCAP / TT)));
+  static constexpr bool VALID = SMEM <= 227 * 1024 && TT <= 1024 && NT % TT == 0 && NT <= 1024;
   static_assert(OFF_BUF % 16 == 0 && OFF_ACC % 16 == 0 && OFF_WS % 16 == 0 && OFF_STG % 16 == 0 &&
                 OFF_S0 % 16 == 0,
                 "column pass shared-memory regions must be 16-byte aligned");
