@@ -52,7 +52,9 @@ typedef enum {
 /* Model and discretisation constants.  Defaults (ttsh_default_params) are Table I:
  * a = 0.5, b = 1.6, lambda = 9, gamma_v = 40, gamma_w = 4, dt = 0.01, N = 8192, dx = 0.005.
  * n must be a power of two in [16, 8192]; precision is 32 (float) or 64 (double) and
- * selects the arithmetic of every kernel of the domain. */
+ * selects the arithmetic of every kernel of the domain.  Double precision has kernels up to
+ * n = 4096 (one row of three double fields at 8192 exceeds a block's shared memory);
+ * ttsh_create_domain returns TTSH_E_UNSUPPORTED for n = 8192 with precision 64. */
 typedef struct {
   double a, b, lambda, gamma_v, gamma_w;
   double dx, dt;
@@ -93,7 +95,8 @@ size_t ttsh_workspace_bytes(const ttsh_params* p);
  * GPU: DFT, zero |m|^2 > (N/8)^2, inverse DFT, square).
  *   mask       host, N*N bytes [y][x]; nonzero = masked (K_naive = 1), 0 = inside.
  *   p          parameters; validated (n power of two in [16, 8192], dx > 0, dt > 0,
- *              precision 32 or 64) -> TTSH_E_INVALID otherwise.
+ *              precision 32 or 64) -> TTSH_E_INVALID otherwise; n = 8192 with precision
+ *              64 -> TTSH_E_UNSUPPORTED.
  *   workspace  device pointer of ttsh_workspace_bytes(p) bytes owned by the caller (it
  *              must outlive the domain), or NULL to let the library cudaMalloc it.
  *   stream     cudaStream_t the domain's kernels are issued on (NULL = legacy default).
@@ -159,8 +162,8 @@ ttsh_status ttsh_diagnostics(ttsh_domain* d, ttsh_diag* out, double* spectrum, i
  * ceil(nsteps / every) samples) is sampled inside that step's row pass, which already holds
  * omega, v_x and v_y in real space.  Sample j is written to series[5 j .. 5 j + 4] =
  * {step count, energy, enstrophy, psi, number of non-finite points}, with the definitions of
- * ttsh_diag; per-thread partial sums are taken in the domain precision and combined in
- * double in a fixed order (repeatable bits).  To record the state after the last step, call
+ * ttsh_diag; per-thread and per-warp partial sums are taken in the domain precision and
+ * the warps' sums combined in double, all in a fixed order (repeatable bits).  To record the state after the last step, call
  * ttsh_diagnostics afterwards.
  *   every     >= 1 steps between samples.
  *   series    device (or managed) memory of at least 5 * capacity doubles, owned by the
