@@ -108,7 +108,8 @@ ttsh_status ttsh_create_domain(const uint8_t* mask, const ttsh_params* p, void* 
 /* Release the domain (and its workspace if the library allocated it).  NULL is a no-op. */
 void ttsh_destroy_domain(ttsh_domain* d);
 
-/* Change the stream later kernels are issued on. */
+/* Change the stream later kernels are issued on; work already queued on the previous
+ * stream is ordered before them by a device-side wait (the host does not block). */
 ttsh_status ttsh_set_stream(ttsh_domain* d, void* stream);
 
 /* Set the state from a real velocity field (host, N*N doubles each).  The field is

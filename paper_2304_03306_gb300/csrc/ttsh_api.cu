@@ -360,10 +360,13 @@ ttsh_status build_graph(ttsh_domain* d) {
 
 // Device status word: a kernel whose bounded wait ran out set it; report it once.
 ttsh_status check_status(ttsh_domain* d) {
+  // on the domain's stream: kernels there may run on a non-blocking stream, which the legacy
+  // default stream does not order against
   int h = 0;
-  TTSH_CUDA(cudaMemcpy(&h, d->dev.err, sizeof(int), cudaMemcpyDeviceToHost), "read status word");
+  TTSH_CUDA(cudaMemcpyAsync(&h, d->dev.err, sizeof(int), cudaMemcpyDeviceToHost, d->stream), "read status word");
+  TTSH_CUDA(cudaStreamSynchronize(d->stream), "read status word");
   if (h) {
-    cudaMemset(d->dev.err, 0, sizeof(int));
+    TTSH_CUDA(cudaMemsetAsync(d->dev.err, 0, sizeof(int), d->stream), "clear status word");
     return fail(TTSH_E_TIMEOUT, "a bounded wait in a kernel ran out (results of the affected steps are not valid)");
   }
   return TTSH_OK;
@@ -925,7 +928,17 @@ void ttsh_destroy_domain(ttsh_domain* d) {
 
 ttsh_status ttsh_set_stream(ttsh_domain* d, void* stream) {
   if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
-  d->stream = static_cast<cudaStream_t>(stream);
+  cudaStream_t ns = static_cast<cudaStream_t>(stream);
+  if (ns != d->stream) {
+    // work already queued on the old stream comes first (device-side wait)
+    cudaEvent_t ev = nullptr;
+    TTSH_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "stream switch");
+    cudaError_t e = cudaEventRecord(ev, d->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ns, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cuda_fail(e, "stream switch");
+    d->stream = ns;
+  }
   return TTSH_OK;
 }
 

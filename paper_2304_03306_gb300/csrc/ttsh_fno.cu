@@ -762,9 +762,10 @@ unsigned tc_grid(long long P) {
 // Report (once) a tensor-core completion wait that ran out; called at synchronising entries.
 ttsh_status check_tc(ttsh_fno* f) {
   int h = 0;
-  FNO_CUDA(cudaMemcpy(&h, f->tc_err, sizeof(int), cudaMemcpyDeviceToHost), "read tensor-core status");
+  FNO_CUDA(cudaMemcpyAsync(&h, f->tc_err, sizeof(int), cudaMemcpyDeviceToHost, f->stream), "read tensor-core status");
+  FNO_CUDA(cudaStreamSynchronize(f->stream), "read tensor-core status");
   if (h) {
-    cudaMemset(f->tc_err, 0, sizeof(int));
+    FNO_CUDA(cudaMemsetAsync(f->tc_err, 0, sizeof(int), f->stream), "clear tensor-core status");
     return fno_fail(TTSH_E_TIMEOUT, "a tensor-core completion wait ran out");
   }
   return TTSH_OK;
@@ -1042,7 +1043,7 @@ ttsh_status ttsh_fno_create(const ttsh_fno_config* cfg, uint64_t seed, void* str
   A(&f->wpart, (long long)f->nwblk * (C * C + C) * 4);
   A(&f->lpart, ((P + 255) / 256) * 8);
   A(&f->tc_err, 64);
-  if (e == cudaSuccess) e = cudaMemset(f->tc_err, 0, 64);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->tc_err, 0, 64, f->stream);
   if (e != cudaSuccess) return cleanup(fno_cuda(e, "FNO allocation"));
   // the fused column kernel needs its plan in shared memory
   if (column_fwd_mix_smem(n) <= 220 * 1024 && row_dft_smem(n, m) <= 220 * 1024 && 2 * m <= 64 &&
@@ -1102,9 +1103,9 @@ ttsh_status ttsh_fno_create(const ttsh_fno_config* cfg, uint64_t seed, void* str
     }
     uni(f->off_Wq, C, -1.0 / sqrt((double)C), 1.0 / sqrt((double)C));
     e = cudaMemcpy(f->theta, th.data(), th.size() * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(f->adam_m, 0, f->nparams * 4);
-    if (e == cudaSuccess) e = cudaMemset(f->adam_v, 0, f->nparams * 4);
-    if (e == cudaSuccess) e = cudaMemset(f->grad, 0, f->nparams * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->adam_m, 0, f->nparams * 4, f->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->adam_v, 0, f->nparams * 4, f->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(f->grad, 0, f->nparams * 4, f->stream);
     if (e == cudaSuccess) e = refresh_bf16(f);
     if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
     if (e != cudaSuccess) return cleanup(fno_cuda(e, "FNO initialisation"));

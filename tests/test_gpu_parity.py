@@ -351,6 +351,27 @@ def test_bounded_wait_timeout_is_reported_once_and_the_domain_stays_usable(T):
     check_fields(dom, O.run(s, K, p, 15), TOL[32])
 
 
+def test_stream_switch_keeps_order_and_results(T):
+    """Work queued on the old stream runs before work issued after ttsh_set_stream."""
+    import torch
+    n, dx = 64, 0.25
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    mask = ti.circle_mask(n, dx, 5.2)
+    vx, vy = ti.noise_velocity(mask, 3, 0.3)
+    a = T.Domain(mask, n, dx, precision=32, stream=s1.cuda_stream)
+    b = T.Domain(mask, n, dx, precision=32)
+    a.set_velocity(vx, vy)
+    b.set_velocity(vx, vy)
+    a.step(300)
+    a.set_stream(s2.cuda_stream)
+    a.step(40)
+    b.step(340)
+    a.synchronize()
+    wa, va = a.spectral_state()
+    wb, vb = b.spectral_state()
+    assert np.array_equal(wa, wb) and np.array_equal(va, vb)
+
+
 # ------------------------------------------------------- checkpoint / graphs
 
 @pytest.mark.parametrize("prec", [32, 64])
