@@ -101,3 +101,30 @@ def test_binding_rejects_mis_shaped_arrays_before_the_call():
         n = 64
     with pytest.raises(ValueError):
         ttsh.Lyapunov(FakeDomain(), np.zeros((2, 100)), 1e-3)
+
+
+def test_every_entry_point_rejects_null_handles(lib):
+    """Each entry point of the header, called with NULL for every pointer and handle (and 1
+    for every number), returns TTSH_E_INVALID (or -1 / 0 for the counting getters, nothing
+    for the destroy functions) before touching the GPU."""
+    from paper_2304_03306_gb300 import ttsh
+    special = {"ttsh_batch_groups": -1, "ttsh_fno_num_params": -1, "ttsh_step_count": -1,
+               "ttsh_workspace_bytes": 0}
+    skip = {"ttsh_default_params", "ttsh_last_error"}
+    for name in declared_functions():
+        if name in skip:
+            continue
+        fn = getattr(lib, name)
+        args = []
+        for t in fn.argtypes:
+            if t in (ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64):
+                args.append(1)
+            elif t in (ctypes.c_double, ctypes.c_float):
+                args.append(1.0)
+            else:
+                args.append(None)
+        r = fn(*args)
+        if fn.restype is None:
+            assert r is None, name
+        else:
+            assert r == special.get(name, ttsh.TTSH_E_INVALID), (name, r)
