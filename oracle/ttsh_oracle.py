@@ -30,7 +30,7 @@ Readings where the paper is silent or inconsistent (also listed in the design no
 * c12 Psi sums over every grid point, e_theta(centre) := 0.
 
 Every function cites the passage it follows.  There is no blocking, fusion or reordering
-beyond what Algorithm 1 states.
+beyond what the scheme of Appendix D states.
 """
 from __future__ import annotations
 
@@ -57,7 +57,7 @@ class Params:
 
 @dataclass
 class State:
-    """Algorithm 1's REQUIRE pair (v(t), omega^(t)): real velocity and vorticity spectrum."""
+    """The scheme's state at time t: real velocity v and vorticity spectrum omega^."""
     vx: np.ndarray      # real (n, n), indexed [y][x]
     vy: np.ndarray      # real (n, n)
     w_hat: np.ndarray   # complex (n, n), FFT order, indexed [ky][kx]
@@ -141,7 +141,9 @@ def process_mask(k_naive: np.ndarray, dft=dft2, idft=idft2) -> np.ndarray:
 # ----------------------------------------------------------------------------------------
 
 def _post_process(w_naive, v0_new, p: Params):
-    """Algorithm 1's FOR ALL k block: k = 0, dealias, Hermitian average, stream function.
+    """Projection that ends every step (Appendix D): omega^(0) = 0 with the mean flow v^(0)
+    from Eq. (avg), removal of the modes beyond the 1/2 rule, the Hermitian average, and the
+    velocity from the stream function, psi^ = omega^/k^2, v^ = (i ky psi^, -i kx psi^).
 
     Returns (omega^_new, v^x_new, v^y_new) on the full FFT-ordered grid.
     """
@@ -168,31 +170,55 @@ def _post_process(w_naive, v0_new, p: Params):
     return w_new, vx_new, vy_new
 
 
+def linear_rate(k2: np.ndarray, p: Params) -> np.ndarray:
+    """Growth rate of the linear part of Eq. (mod2) at |k|^2 = k2: a - (1 - k^2)^2 (the
+    Swift-Hohenberg operator a - (1 + nabla^2)^2 in Fourier space)."""
+    return p.a - (1.0 - k2) ** 2
+
+
+def nonlinear_terms(vx, vy, omega, gx, gy, K, p: Params):
+    """The non-linear and mask terms of Eq. (mod2) in real space, before the curl.
+
+    Velocity-level part (its curl enters the vorticity equation; Sec. II.A):
+        f_v = -b |v|^2 v - gamma_v K v
+    Vorticity-level part, with grad(omega) = (gx, gy):
+        f_w = -lambda v . grad(omega) - gamma_w K omega
+    """
+    v2 = vx * vx + vy * vy
+    fvx = -p.b * v2 * vx - p.gamma_v * K * vx
+    fvy = -p.b * v2 * vy - p.gamma_v * K * vy
+    fw = -p.lam * (vx * gx + vy * gy) - p.gamma_w * K * omega
+    return fvx, fvy, fw
+
+
 def step(s: State, K: np.ndarray, p: Params, dft=dft2, idft=idft2) -> State:
-    """One step of Algorithm 1 for Eq. (mod2); returns (v(t+dt), omega^(t+dt))."""
+    """One time step of Eq. (mod2) with the pseudospectral integrating-factor Euler scheme of
+    Appendix D: the linear operator is integrated exactly over dt, the non-linear and mask
+    terms by forward Euler, then the k = 0 mean flow follows the space-averaged equation
+    Eq. (avg) and the spectrum is projected (Hermitian, 1/2 rule, stream-function velocity).
+    Returns (v(t+dt), omega^(t+dt))."""
     KX, KY, _ = wavenumbers(p)
     vx, vy, w_hat = s.vx, s.vy, s.w_hat
-    omega = np.real(idft(w_hat))                      # reading c7
-    # line 1: rhs1 = -b |v|^2 v - gamma_v K v
-    v2 = vx * vx + vy * vy
-    rhs1x = -p.b * v2 * vx - p.gamma_v * K * vx
-    rhs1y = -p.b * v2 * vy - p.gamma_v * K * vy
-    # line 2: rhs2 = -lambda v . iDFT[i k omega^] - gamma_w K omega
+    # real-space fields the non-linear terms need; nabla <-> +ik (reading c1), real parts
+    # (reading c7)
+    omega = np.real(idft(w_hat))
     gx = np.real(idft(1j * KX * w_hat))
     gy = np.real(idft(1j * KY * w_hat))
-    rhs2 = -p.lam * (vx * gx + vy * gy) - p.gamma_w * K * omega
-    # line 3: rhs^ = i k x rhs^_1 + rhs^_2   (z-component of the curl: i(kx R1y - ky R1x))
-    R1x, R1y, R2 = dft(rhs1x), dft(rhs1y), dft(rhs2)
-    rhs_hat = 1j * (KX * R1y - KY * R1x) + R2
-    # line 4: integrating factor exp[(a - (1 - k^2)^2) dt] applied to the Euler update
+    fvx, fvy, fw = nonlinear_terms(vx, vy, omega, gx, gy, K, p)
+    # Fourier transform of the vorticity equation's non-linear part: the z-component of the
+    # curl of f_v, i(kx f^_vy - ky f^_vx), plus f^_w
+    Fvx, Fvy, Fw = dft(fvx), dft(fvy), dft(fw)
+    n_hat = 1j * (KX * Fvy - KY * Fvx) + Fw
+    # integrating-factor Euler: omega^ <- exp(L(k) dt) (omega^ + dt N^(k))
     k2 = KX * KX + KY * KY
-    w_naive = np.exp((p.a - (1.0 - k2) ** 2) * p.dt) * (w_hat + rhs_hat * p.dt)
-    # line 8: v^_new(0) = exp[(a - 1) dt] sum_x N^-1 (v + rhs1 dt)
+    w_naive = np.exp(linear_rate(k2, p) * p.dt) * (w_hat + n_hat * p.dt)
+    # k = 0 (Eq. avg): the mean flow obeys d<v>/dt = (a - 1)<v> + <f_v>; the same scheme
+    # gives v^(0) <- exp((a - 1) dt) DFT[v + dt f_v](0)
     g0 = np.exp((p.a - 1.0) * p.dt)
-    v0x = g0 * np.real(dft(vx + rhs1x * p.dt)[0, 0])
-    v0y = g0 * np.real(dft(vy + rhs1y * p.dt)[0, 0])
+    v0x = g0 * np.real(dft(vx + fvx * p.dt)[0, 0])
+    v0y = g0 * np.real(dft(vy + fvy * p.dt)[0, 0])
     w_new, vx_hat, vy_hat = _post_process(w_naive, (v0x, v0y), p)
-    # ENSURE: (v_new, omega^_new), v_new = iDFT[v^_new]
+    # the new velocity in real space, from its (stream-function) spectrum
     return State(np.real(idft(vx_hat)), np.real(idft(vy_hat)), w_new)
 
 
@@ -205,7 +231,7 @@ def run(s: State, K: np.ndarray, p: Params, nsteps: int, **kw) -> State:
 def project_velocity(vx: np.ndarray, vy: np.ndarray, p: Params, dft=dft2, idft=idft2) -> State:
     """Initial state from a real velocity field (reading c6).
 
-    omega^ = i k x v^ = i(kx v^y - ky v^x); then Algorithm 1's FOR ALL k block with
+    omega^ = i k x v^ = i(kx v^y - ky v^x); then the projection that ends each step with
     v^(0) = DFT[v](0), which zeroes omega^(0), dealiases, Hermitian-averages and rebuilds v
     from the stream function, so the state is divergence-free and band-limited.
     """

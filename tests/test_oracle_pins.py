@@ -374,6 +374,47 @@ def test_vortex_order_parameter_limits():
     assert psi_rad == pytest.approx(-(2 / np.pi) / (1 - 2 / np.pi), abs=1e-14)
 
 
+def test_vortex_order_parameter_about_an_off_grid_centre():
+    """Solid-body rotation about a centre that is no grid point: v = (-(y - y0), x - x0) is
+    purely azimuthal about (x0, y0), so |e_theta . v| = |v| at every point and Psi = 1
+    exactly.  Measured about the box origin instead, or with the centre offset taken with the
+    wrong sign on either axis, the same field has a radial part and Psi drops well below 1."""
+    p = O.Params(n=64, dx=0.25)
+    X, Y = coords(p)
+    x0, y0 = 0.37, -0.61                    # between grid points on both axes
+    vx, vy = -(Y - y0), X - x0
+    assert O.vortex_order_parameter(vx, vy, p, center=(x0, y0)) == pytest.approx(1.0, abs=1e-13)
+    for wrong in [(0.0, 0.0), (-x0, y0), (x0, -y0), (y0, x0)]:
+        assert O.vortex_order_parameter(vx, vy, p, center=wrong) < 0.99
+
+
+def test_vortex_order_parameter_at_the_centre_point():
+    """Reading c12: at the centre itself e_theta := 0, so a velocity there adds |v| to the
+    denominator only.  Field zero everywhere except v = (0.3, -0.4) at the grid point that is
+    the centre: sum|e_theta . v| = 0, sum|v| = 0.5, Psi = (0 - 2/pi) / (1 - 2/pi).  Adding a
+    unit azimuthal velocity at one other point gives ratio 1/1.5.  The centre is a grid point
+    away from the box origin, so its index must come from the offset with the right sign."""
+    p = O.Params(n=32, dx=0.5)
+    i0, j0 = 11, 23                         # row (y) and column (x) of the centre point
+    c = (np.arange(p.n) - p.n // 2) * p.dx
+    centre = (c[j0], c[i0])
+    vx = np.zeros((p.n, p.n))
+    vy = np.zeros((p.n, p.n))
+    vx[i0, j0], vy[i0, j0] = 0.3, -0.4
+    two_pi = 2 / np.pi
+    assert O.vortex_order_parameter(vx, vy, p, center=centre) == pytest.approx(
+        (0.0 - two_pi) / (1 - two_pi), abs=1e-14)
+    # one more point, 3 cells to the right of the centre (+x): e_theta there is (0, 1)
+    vy[i0, j0 + 3] = 1.0
+    assert O.vortex_order_parameter(vx, vy, p, center=centre) == pytest.approx(
+        (1.0 / 1.5 - two_pi) / (1 - two_pi), abs=1e-14)
+    # the same field about a centre one cell off: the centre point's velocity now counts
+    # in the numerator (its e_theta is a unit vector), so Psi differs
+    off = (c[j0 + 1], c[i0])
+    assert abs(O.vortex_order_parameter(vx, vy, p, center=off) -
+               (1.0 / 1.5 - two_pi) / (1 - two_pi)) > 1e-3
+
+
 # ------------------------------------------------------------ inputs / constants
 
 def test_table1_constants_match_golden():
