@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-lyap", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2048^2 and 8192^2 legs")
     ap.add_argument("--plan", default=None, metavar="ROW,COL[,MODE]",
                     help="float32 step-kernel variants and launch mode instead of the autotuner's choice")
     return ap.parse_args()
@@ -201,23 +202,58 @@ def ncu_executed(kernel, n, precision, plan):
 
 # ----------------------------------------------------------------------- CPU oracle leg
 
-def time_oracle(w, record_every, budget_s=10.0, min_steps=3):
+def _oracle_replica(wname, record_every, warm_steps, timed_steps, budget_s, barrier, out):
+    """One single-threaded oracle process stepping its own copy of the workload: set-up and
+    warm-up, then (after every replica is ready) `timed_steps` steps, or as many as fit in
+    `budget_s` seconds when timed_steps is 0.  Puts (steps, seconds) on `out`."""
     from oracle import ttsh_oracle as O
+    w = ti.WORKLOADS[wname]
     n, dx = w["n"], w["dx"]
     mask = ti.circle_mask(n, dx, w["radius"])
     vx, vy = ti.noise_velocity(mask, w["seed"], 0.01)
     p = O.Params(n=n, dx=dx)
     K = O.process_mask(mask)
     s = O.project_velocity(vx, vy, p)
-    s = O.step(s, K, p)   # warm
-    steps, t0 = 0, time.perf_counter()
-    while steps < min_steps or time.perf_counter() - t0 < budget_s:
-        if record_every > 0 and steps % record_every == 0:
+    count = 0
+
+    def one(s, count):
+        if record_every > 0 and count % record_every == 0:
             O.diagnostics(s, p)
-        s = O.step(s, K, p)
+        return O.step(s, K, p), count + 1
+
+    for _ in range(max(1, warm_steps)):
+        s, count = one(s, count)
+    barrier.wait()
+    t0 = time.perf_counter()
+    steps = 0
+    while (timed_steps > 0 and steps < timed_steps) or \
+            (timed_steps == 0 and (steps < 3 or time.perf_counter() - t0 < budget_s)):
+        s, count = one(s, count)
         steps += 1
-    dt = time.perf_counter() - t0
-    return n * n * steps / dt, steps, dt
+    out.put((steps, time.perf_counter() - t0))
+
+
+def oracle_replicas(wname, record_every, procs=None, warm_steps=1, timed_steps=0, budget_s=10.0):
+    """The FP64 oracle as it stands on every host core: `procs` (default: all cores)
+    independent single-threaded processes, each stepping its own copy of the workload, started
+    with the spawn method (no fork after CUDA).  Returns (aggregate grid-point-steps/s, procs,
+    steps per process, wall seconds of the slowest)."""
+    import multiprocessing as mp
+    P = procs or os.cpu_count() or 1
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(P), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_replica, args=(wname, record_every, warm_steps, timed_steps, budget_s,
+                                                       barrier, out)) for _ in range(P)]
+    for q in ps:
+        q.start()
+    res = [out.get() for _ in range(P)]
+    for q in ps:
+        q.join()
+    n = ti.WORKLOADS[wname]["n"]
+    rate = sum(n * n * st / dt for st, dt in res)
+    return rate, P, [st for st, _ in res], max(dt for _, dt in res)
 
 
 # ------------------------------------------------------------------------ GPU leg
@@ -308,6 +344,11 @@ def run_ours(args, rank, world, local_rank):
     diag = dom.diagnostics()
     dom.close()
 
+    # measured FMA throughput of this GPU: the denominators of the ALU rooflines
+    fma_peak = {"fp32_tflops": ttsh.ttsh_fma_peak(32, 1 << 17), "fp64_tflops": ttsh.ttsh_fma_peak(64, 1 << 12),
+                "how": "ttsh_fma_peak: 8 blocks of 256 threads per SM, 8 independent FMA chains per thread, "
+                       "CUDA events"}
+
     # ---- float64 alongside ----
     fp64 = None
     if not args.no_fp64:
@@ -330,12 +371,13 @@ def run_ours(args, rank, world, local_rank):
         fp64 = {"value": v64, "unit": UNIT, "solver_steps_per_step": S64,
                 "ms_per_solver_step": 1e3 * t64 / (S64 * K), "row_pass_ms": r64, "col_pass_ms": c64,
                 "fp32_over_fp64": value / v64, "plan": plan64,
-                "roofline": {"bound": "alu", "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                             "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": ncu_traffic(k64, n, 64, plan64),
+                "roofline": {"bound": "alu", "achieved": ach64, "peak": fma_peak["fp64_tflops"], "unit": "TFLOP/s",
+                             "frac": ach64 / fma_peak["fp64_tflops"], "traffic": ncu_traffic(k64, n, 64, plan64),
                              "kernel": k64, "kernel_ms": ms64, "algorithmic_flops": fl[k64],
                              "executed_flops": ex64,
                              "executed_tflops": None if ex64 is None else ex64 / (ms64 * 1e-3) / 1e12,
-                             "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (nominal FP64 rate)"}}
+                             "peak_source": "measured (ttsh_fma_peak, FP64 FMA chains on every SM)",
+                             "nominal_peak": FP64_PEAK_TFLOPS}}
 
     # ---- batched sweep: 48 domains (128^2..512^2 circles and dumbbells) in lock step ----
     batched = None
@@ -366,6 +408,54 @@ def run_ours(args, rank, world, local_rank):
         bt.close()
         for o in objs:
             o.close()
+
+    # ---- the HBM-bound grids: 2048^2 turbulent circle (FP32 and FP64) and the paper's 8192^2 ----
+    def large_leg(wname, prec, S_l):
+        wl = ti.WORKLOADS[wname]
+        nl, dxl = wl["n"], wl["dx"]
+        ml = ti.circle_mask(nl, dxl, wl["radius"])
+        dl = ttsh.Domain(ml, nl, dxl, precision=prec, stream=stream.cuda_stream)
+        dl.init_noise(wl["seed"] + rank, 0.01)
+        planl = dl.autotune(iters=max(20, min(400, int(4e7 // (nl * nl)))))
+        for _ in range(W):
+            dl.step(S_l)
+        dl.synchronize()
+        barrier()
+        tl = max_over_ranks(timed_segments(dl, K, S_l, record=False))
+        rms, cms = dl.time_kernels(max(20, min(2000, int(2e7 // (nl * nl)))))
+        dl.close()
+        elt_l = 4 if prec == 32 else 8
+        abl = algorithmic_bytes(nl, elt_l)
+        kl = "row_pass" if rms >= cms else "col_pass"
+        msl = max(rms, cms)
+        pk, pk_src = peaks()
+        ach = abl[kl] / (msl * 1e-3) / 1e9
+        vl = world * nl * nl * S_l * K / tl
+        step_bytes = abl["row_pass"] + abl["col_pass"]
+        out = {"workload": workload_desc(wname, wl, S_l), "precision": prec, "value": vl, "unit": UNIT,
+               "ms_per_solver_step": 1e3 * tl / (S_l * K), "plan": planl,
+               "roofline": {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s", "frac": ach / pk,
+                            "traffic": ncu_traffic(kl, nl, prec, planl), "kernel": kl, "kernel_ms": msl,
+                            "algorithmic_bytes": abl[kl], "peak_source": f"{pk_src} (copy bandwidth)",
+                            "passes_ms": {"row_pass": rms, "col_pass": cms}},
+               "step_roofline": {"bytes_per_point": step_bytes / (nl * nl),
+                                 "achieved_gbs": step_bytes * vl / (world * nl * nl) / 1e9,
+                                 "frac": step_bytes * vl / (world * nl * nl) / 1e9 / pk,
+                                 "note": "whole step (both passes and the launch gaps) at the algorithmic bytes"}}
+        if prec == 64:
+            fl = algorithmic_flops(nl)
+            out["alu_roofline"] = {"bound": "alu", "achieved": fl[kl] / (msl * 1e-3) / 1e12,
+                                   "peak": fma_peak["fp64_tflops"], "unit": "TFLOP/s",
+                                   "frac": fl[kl] / (msl * 1e-3) / 1e12 / fma_peak["fp64_tflops"],
+                                   "peak_source": "measured (ttsh_fma_peak)"}
+        return out
+
+    large = None
+    if not args.no_large:
+        large = {"circle2048_fp32": large_leg("circle2048_turbulent", 32, 2000),
+                 "circle8192_fp32": large_leg("circle8192_paper_grid", 32, 100)}
+        if not args.no_fp64:
+            large["circle2048_fp64"] = large_leg("circle2048_turbulent", 64, 100)
 
     # ---- Lyapunov analysis: the workload's domain with 8 perturbed copies ----
     lyap = None
@@ -482,18 +572,21 @@ def run_ours(args, rank, world, local_rank):
                 "step_bytes_per_point": (ab["row_pass"] + ab["col_pass"]) / (n * n)}
     fl32 = algorithmic_flops(n)
     roofline["alu_context"] = {"achieved_tflops": fl32[dom_k] / (dom_ms * 1e-3) / 1e12,
-                               "peak_tflops": FP32_PEAK_TFLOPS,
-                               "frac": fl32[dom_k] / (dom_ms * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                               "peak_tflops": fma_peak["fp32_tflops"],
+                               "frac": fl32[dom_k] / (dom_ms * 1e-3) / 1e12 / fma_peak["fp32_tflops"],
                                "algorithmic_flops": fl32[dom_k],
                                "executed_flops": ncu_executed(dom_k, n, 32, plan32),
-                               "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}
+                               "peak_source": "measured (ttsh_fma_peak, FP32 FMA chains on every SM)",
+                               "nominal_peak_tflops": FP32_PEAK_TFLOPS}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:
-        v, steps, dt = time_oracle(w, RE)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{steps} oracle (numpy FP64, single-threaded) steps of the same {n}x{n} workload in "
-                         f"{dt:.1f} s, oracle diagnostics every {RE} steps"}
+        v, P, steps, dt = oracle_replicas(args.workload, RE)
+        cpu = {"value": v, "unit": UNIT, "cores": P, "kind": "oracle",
+               "sample": f"{P} independent single-threaded oracle processes (numpy FP64, one per host core, "
+                         f"nproc = {os.cpu_count()}), each stepping its own copy of the {n}x{n} workload for "
+                         f"~{dt:.0f} s ({min(steps)}-{max(steps)} steps each), oracle diagnostics every {RE} "
+                         f"steps; value = the sum of the processes' grid-point-steps/s"}
 
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -508,7 +601,8 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e, "gpu_launches": K * (2 * S + (1 if RE > 0 else 0)), "clocks": clk, "roofline": roofline,
         "value_without_time_series": world * n * n * S * K / t_plain,
         "time_series_last_sample": series_last,
-        "cpu_baseline": cpu, "fp64": fp64, "batched": batched, "surrogate": surrogate, "lyapunov": lyap,
+        "cpu_baseline": cpu, "fp64": fp64, "batched": batched, "large_grids": large, "fma_peak": fma_peak,
+        "surrogate": surrogate, "lyapunov": lyap,
         "diagnostics_after": {"energy": diag["energy"], "psi": diag["psi"], "nonfinite": diag["nonfinite"]},
         "ms_per_solver_step": 1e3 * t32 / (K * S),
     }
@@ -519,41 +613,22 @@ def run_reference(args, rank, world):
         return None
     w = ti.WORKLOADS[args.workload]
     n = w["n"]
-    from oracle import ttsh_oracle as O
-    mask = ti.circle_mask(n, w["dx"], w["radius"])
-    vx, vy = ti.noise_velocity(mask, w["seed"], 0.01)
-    p = O.Params(n=n, dx=w["dx"])
-    K_ = O.process_mask(mask)
-    s = O.project_velocity(vx, vy, p)
-    S_ref = max(1, int(2.0e6 // (n * n)))   # ~1 s of oracle work per step at 512^2
+    S_ref = max(1, int(1.0e6 // (n * n)))   # oracle steps per timed step and process (~0.3 s at 512^2)
     RE = args.record_every
-    count = 0
-
-    def segment(s, count):
-        series = []
-        for _ in range(S_ref):
-            if RE > 0 and count % RE == 0:
-                series.append(O.diagnostics(s, p))
-            s = O.step(s, K_, p)
-            count += 1
-        return s, count
-
-    for _ in range(args.warmup):
-        s, count = segment(s, count)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        s, count = segment(s, count)
-    dt = time.perf_counter() - t0
-    v = n * n * S_ref * args.steps / dt
+    # every process warms up for W steps' worth, then all run the K timed steps' worth at once
+    v, P, steps, wall = oracle_replicas(args.workload, RE, warm_steps=S_ref * max(1, args.warmup),
+                                        timed_steps=S_ref * args.steps)
+    v = P * n * n * S_ref * args.steps / wall   # whole job: all processes' points over the slowest's time
+    sample = (f"{P} independent single-threaded oracle processes (one per host core, nproc = {os.cpu_count()}), "
+              f"each {S_ref * args.steps} timed oracle steps of its own copy of the {n}x{n} workload")
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, w, S_ref), "n": n,
-                       "solver_steps_per_step": S_ref, "parallelism": "replicas",
+                       "solver_steps_per_step": S_ref, "parallelism": f"{P} CPU processes (replicas)",
                        "time_series": f"oracle diagnostics every {RE} solver steps" if RE > 0 else "none"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{S_ref * args.steps} oracle steps of the {n}x{n} workload"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": P, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

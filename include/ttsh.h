@@ -69,10 +69,14 @@ typedef struct {
  *   psi       = vortex order parameter of Sec. III.C: (sum|e_theta.v| / sum|v| - 2/pi)
  *               / (1 - 2/pi) over every grid point, about the given centre (e_theta := 0
  *               at the centre itself)
+ *   max_div   = max |k.v^(m)| / max |k| |v^(m)| over the modes of the 1/2-rule disc, where
+ *               v^ = DFT[v] of the real-space velocity the row pass works with (the
+ *               incompressibility div v = 0 that the stream-function construction of
+ *               Appendix D guarantees; round-off level: ~1e-16 double, ~1e-7 float)
  *   mean_vx, mean_vy = spatial mean of v (= v^(0) / N)
  *   nonfinite = number of non-finite values met in the state's real-space fields. */
 typedef struct {
-  double energy, enstrophy, psi, mean_vx, mean_vy;
+  double energy, enstrophy, psi, max_div, mean_vx, mean_vy;
   int64_t step;
   int32_t nonfinite;
   int32_t reserved;
@@ -123,15 +127,27 @@ ttsh_status ttsh_set_velocity(ttsh_domain* d, const double* vx, const double* vy
  * 8-byte-aligned device pointers, read during the call only). */
 ttsh_status ttsh_set_velocity_device(ttsh_domain* d, const double* vx, const double* vy);
 
-/* Advance the state by nsteps steps of Algorithm 1 (Appendix D): real-space nonlinear and
- * mask terms (lines 1-2; the advection v.grad(omega) is evaluated in its conservative form
- * div(v omega), which equals it on every kept mode up to rounding because v and omega are
- * band-limited to the 1/2-rule disc and div v = 0), DFT of the right-hand side and curl
- * assembly (line 3), the
- * integrating-factor Euler update (line 4), the k = 0 mean-flow update of Eq. (avg)
- * (lines 6-8), the 1/2-rule dealiasing (lines 9-11), the Hermitian average and the
- * stream-function velocity (lines 13-15).  Asynchronous on the domain's stream; long runs
- * are replayed as CUDA graphs.  nsteps < 0 -> TTSH_E_INVALID; 0 is a no-op. */
+/* Set the state to the paper's "random initial state" (Sec. III.A and Sec. IV.A), generated
+ * on the device: at every point inside the domain (mask byte 0 in the mask given to
+ * ttsh_create_domain) v_x and v_y are independent draws, uniform on [-amplitude, amplitude),
+ * and 0 at masked points; then projected as ttsh_set_velocity does.  The draws come from
+ * the SplitMix64 generator (Steele, Lea & Flood 2014) in counter form: at flattened point
+ * p = y N + x, v_x uses output 2p and v_y output 2p + 1 of the stream seeded with `seed`,
+ * an output z giving u = (z >> 11) 2^-53 and the value amplitude (2u - 1) in double
+ * precision.  The same seed therefore gives the same field, bit for bit, as any other
+ * implementation of that definition, on any grid size.  amplitude must be finite
+ * (TTSH_E_INVALID otherwise).  Resets the step counter; synchronises. */
+ttsh_status ttsh_init_noise(ttsh_domain* d, uint64_t seed, double amplitude);
+
+/* Advance the state by nsteps steps of the pseudospectral integrating-factor Euler scheme
+ * of Appendix D (Algorithm 1) for Eq. (mod2): the real-space non-linear and mask terms (the
+ * advection v.grad(omega) is evaluated in its conservative form div(v omega), which equals
+ * it on every kept mode up to rounding because v and omega are band-limited to the
+ * 1/2-rule disc and div v = 0), the DFT of those terms and their curl, the integrating-
+ * factor Euler update omega^ <- exp((a - (1 - k^2)^2) dt)(omega^ + dt rhs^), the k = 0
+ * mean-flow update of Eq. (avg), the 1/2-rule dealiasing, the Hermitian average and the
+ * stream-function velocity.  Asynchronous on the domain's stream; long runs are replayed as
+ * CUDA graphs.  nsteps < 0 -> TTSH_E_INVALID; 0 is a no-op. */
 ttsh_status ttsh_step(ttsh_domain* d, int64_t nsteps);
 
 /* Copy the real-space fields of the current state to the host (N*N doubles each, [y][x]):
@@ -231,11 +247,14 @@ ttsh_status ttsh_set_launch_mode(ttsh_domain* d, int32_t mode);
  * Scratch (inter-pass buffers, twiddle tables) lives in one fixed device array inside the
  * library, sized for n <= 512 (about 6.4 MB, held by every GPU that loads the library until
  * the process exits); n > 512 -> TTSH_E_INVALID, as are the parameter checks of
- * ttsh_create_domain.  The first call on each device resolves that array's address and
- * writes its twiddle tables (synchronous copies); make that first call before any stream
- * capture.  All calls share the array, so calls that overlap on the GPU race: serialise
- * them.  Kernels are issued on `stream` (NULL = legacy default) and the call returns without
- * waiting for them. */
+ * ttsh_create_domain.  The first call on each device resolves that array's address, writes
+ * its twiddle tables and waits for the whole device (cudaDeviceSynchronize) so that the
+ * tables are in place before any kernel on any stream reads them; make that first call
+ * before any stream capture.  All calls share the array, so calls that overlap on the GPU
+ * race: serialise them.  Kernels are issued on `stream` (NULL = legacy default) and the call
+ * returns without waiting for them.  A bounded wait inside the kernels that ran out (a lost
+ * bulk-copy completion) is not reported by this entry point; the domain path reports it as
+ * TTSH_E_TIMEOUT. */
 ttsh_status ttsh_step_noalloc(const ttsh_params* p, const void* K, void* w_hat, void* v0,
                               int64_t nsteps, void* stream);
 
@@ -375,6 +394,13 @@ ttsh_status ttsh_fno_rollout(ttsh_fno* f, ttsh_domain* d, int64_t nsteps, int32_
  * the next ttsh_synchronize returns TTSH_E_TIMEOUT once; the CUDA context and the domain
  * stay usable.  (Production waits are limited to 2 s.) */
 ttsh_status ttsh_test_bounded_wait(ttsh_domain* d, double seconds);
+
+/* Measured arithmetic peak of the current GPU, for roofline reports (no counterpart in the
+ * paper): one launch of a probe kernel in which every thread of 8 blocks of 256 per SM runs 8
+ * independent fused multiply-add chains for `iters` iterations in the given precision (32 or
+ * 64), timed with CUDA events; *tflops = 2 x chains x iters x threads / time.  iters in
+ * [1, 2^24] (TTSH_E_INVALID otherwise).  Synchronises its own stream; allocates 8 bytes. */
+ttsh_status ttsh_fma_peak(int32_t precision, int32_t iters, double* tflops);
 
 /* Block the host until the domain's stream is idle; reports deferred CUDA errors, and
  * TTSH_E_TIMEOUT (once) if a bounded wait inside a kernel ran out since the last report (the

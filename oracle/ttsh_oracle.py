@@ -80,6 +80,24 @@ def idft2(F: np.ndarray) -> np.ndarray:
     return np.fft.ifft2(F, norm="ortho")
 
 
+def threaded_dft(workers: int | None = None):
+    """The same unitary DFT pair computed by scipy.fft on `workers` threads (default: every
+    host core) - a library primitive like numpy's pocketfft, for running the oracle at large
+    grid sizes in tests.  Returns (dft, idft) to pass to the functions below."""
+    import os
+
+    import scipy.fft as sf
+    w = workers or os.cpu_count() or 1
+
+    def dft(f):
+        return sf.fft2(f, norm="ortho", workers=w)
+
+    def idft(F):
+        return sf.ifft2(F, norm="ortho", workers=w)
+
+    return dft, idft
+
+
 def _dft_matrix(n: int, sign: int) -> np.ndarray:
     j = np.arange(n)
     return np.exp(sign * 2j * np.pi * np.outer(j, j) / n)

@@ -56,7 +56,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 struct Layout {
-  size_t what, vmean, K, G, Rr, tw, real, part, colhist, bad, out, save, rec, recctl, err, total;
+  size_t what, vmean, K, G, Rr, tw, real, part, colhist, bad, out, save, rec, recctl, err, knaive, total;
 };
 
 Layout layout_for(int n, size_t elt) {
@@ -84,6 +84,7 @@ Layout layout_for(int n, size_t elt) {
   L.rec = take((size_t)n * ttsh::kDiagQ * sizeof(double));   // time-series partials (<= n row blocks)
   L.recctl = take(64);                                        // time-series write position
   L.err = take(64);                                           // device status word
+  L.knaive = take(NN);                                        // binary mask as given (ttsh_init_noise)
   static_assert(sizeof(ttsh::RecCtl) <= 64, "RecCtl must fit its region");
   L.total = off;
   return L;
@@ -430,6 +431,38 @@ cudaError_t launch_spectrum_reduce(const double* colhist, int ncols, int nbins, 
   return cudaGetLastError();
 }
 
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) in counter form: output i of the stream
+// started at `seed` is the 64-bit finaliser applied to seed + (i + 1) * 0x9E3779B97F4A7C15.
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long i) {
+  unsigned long long z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// The initial velocity of the paper's runs, a "random initial state" (Sec. III.A): at every
+// point inside the domain (K_naive = 0) v_x and v_y are i.i.d. uniform on [-A, A), v_x from
+// draw 2p and v_y from draw 2p + 1 of point p = y N + x; a draw z gives u = (z >> 11) 2^-53
+// in [0, 1) and A (2u - 1).  Masked points get 0.  Written to the double staging planes 0
+// and 1, which the projection of the initial state reads; explicit roundings, so the values
+// are the same bits as any other implementation of this definition in double precision.
+__global__ void noise_kernel(double* __restrict__ real, const unsigned char* __restrict__ knaive, long long nn,
+                             unsigned long long seed, double amp) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nn; p += stride) {
+    double vx = 0.0, vy = 0.0;
+    if (knaive[p] == 0) {
+      const unsigned long long i = 2ull * (unsigned long long)p;
+      const double ux = (double)(splitmix64_at(seed, i) >> 11) * 0x1.0p-53;
+      const double uy = (double)(splitmix64_at(seed, i + 1) >> 11) * 0x1.0p-53;
+      vx = __dmul_rn(amp, __dsub_rn(__dmul_rn(2.0, ux), 1.0));
+      vy = __dmul_rn(amp, __dsub_rn(__dmul_rn(2.0, uy), 1.0));
+    }
+    real[p] = vx;
+    real[nn + p] = vy;
+  }
+}
+
 __global__ void record_begin_kernel(RecCtl* c, long long base, double* series, long long capacity,
                                     int every, int nblocks, double inv2n2) {
   c->count = 0;
@@ -512,6 +545,7 @@ int domain_clone(const ttsh_domain* src, ttsh_domain** out) {
   v.rec = nullptr;
   v.recctl = nullptr;
   v.err = reinterpret_cast<int*>(base + d->lay.err);
+  v.knaive = reinterpret_cast<unsigned char*>(base + d->lay.knaive);
   init_tensor_maps(v, d->n, d->elt);
   const size_t NN = (size_t)d->n * d->n;
   const size_t wbytes = (size_t)d->H * d->NK * 2 * d->elt;
@@ -521,6 +555,7 @@ int domain_clone(const ttsh_domain* src, ttsh_domain** out) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.tw, src->dev.tw, (size_t)d->n * 2 * d->elt, cudaMemcpyDeviceToDevice, d->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.what, src->dev.what, wbytes, cudaMemcpyDeviceToDevice, d->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(v.vmean, src->dev.vmean, 64, cudaMemcpyDeviceToDevice, d->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v.knaive, src->dev.knaive, NN, cudaMemcpyDeviceToDevice, d->stream);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "clone copies"));
   ttsh_status st = run_col(d, K_COL_PROLOGUE, d->stream);
   if (st != TTSH_OK) return cleanup(st);
@@ -871,6 +906,7 @@ ttsh_status ttsh_create_domain(const uint8_t* mask, const ttsh_params* p, void* 
   v.pdl = 0;
   v.use_tma = 0;
   v.err = reinterpret_cast<int*>(base + d->lay.err);
+  v.knaive = reinterpret_cast<unsigned char*>(base + d->lay.knaive);
   init_tensor_maps(v, d->n, d->elt);
   {
     cudaError_t e = cudaMemsetAsync(v.err, 0, 64, d->stream);
@@ -894,8 +930,13 @@ ttsh_status ttsh_create_domain(const uint8_t* mask, const ttsh_params* p, void* 
   // Algorithm 2 on the device: K_naive (0/1) -> DFT -> |m|^2 <= (N/8)^2 -> iDFT -> square.
   {
     std::vector<double> kn(NN);
-    for (size_t i = 0; i < NN; ++i) kn[i] = mask[i] ? 1.0 : 0.0;
+    std::vector<unsigned char> kb(NN);
+    for (size_t i = 0; i < NN; ++i) {
+      kn[i] = mask[i] ? 1.0 : 0.0;
+      kb[i] = mask[i] ? 1 : 0;
+    }
     cudaError_t e = cudaMemcpyAsync(v.real, kn.data(), NN * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(v.knaive, kb.data(), NN, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cleanup(cuda_fail(e, "mask upload"));
   }
@@ -955,6 +996,17 @@ ttsh_status ttsh_set_velocity_device(ttsh_domain* d, const double* vx, const dou
   const size_t NN = (size_t)d->n * d->n;
   TTSH_CUDA(cudaMemcpyAsync(d->dev.real, vx, NN * sizeof(double), cudaMemcpyDeviceToDevice, d->stream), "copy vx");
   TTSH_CUDA(cudaMemcpyAsync(d->dev.real + NN, vy, NN * sizeof(double), cudaMemcpyDeviceToDevice, d->stream), "copy vy");
+  return project_staged(d);
+}
+
+ttsh_status ttsh_init_noise(ttsh_domain* d, uint64_t seed, double amplitude) {
+  if (!d) return fail(TTSH_E_INVALID, "domain is NULL");
+  if (!std::isfinite(amplitude)) return fail(TTSH_E_INVALID, "amplitude must be finite");
+  const long long nn = (long long)d->n * d->n;
+  const int blocks = (int)std::min<long long>((nn + 255) / 256, 152LL * 16);
+  ttsh::noise_kernel<<<blocks, 256, 0, d->stream>>>(d->dev.real, d->dev.knaive, nn, (unsigned long long)seed,
+                                                     amplitude);
+  TTSH_CUDA(cudaGetLastError(), "noise kernel");
   return project_staged(d);
 }
 
@@ -1139,6 +1191,10 @@ ttsh_status ttsh_diagnostics(ttsh_domain* d, ttsh_diag* out, double* spectrum, i
   TTSH_CUDA(d->ops.spec(d->dev, nb_dev, s), "spectrum kernel");
   const double scale = 1.0 / (2.0 * (double)d->n * (double)d->n);
   TTSH_CUDA(ttsh::launch_spectrum_reduce(d->dev.colhist, d->H, nb_dev, scale, d->dev.out + 8, s), "spectrum reduce");
+  // divergence of the real-space velocity: the diagnostic row pass left DFT_x[v_x], DFT_x[v_y]
+  // in the inter-pass buffer; the column pass completes the transforms and takes the maxima
+  TTSH_CUDA(cudaMemsetAsync(d->dev.out + 5, 0, 2 * sizeof(double), s), "memset");
+  if ((st = run_col(d, ttsh::K_COL_DIV, s)) != TTSH_OK) return st;
   std::vector<double> h(8 + nb_dev);
   int bad = 0;
   TTSH_CUDA(cudaMemcpyAsync(h.data(), d->dev.out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s), "download diag");
@@ -1159,6 +1215,7 @@ ttsh_status ttsh_diagnostics(ttsh_domain* d, ttsh_diag* out, double* spectrum, i
   out->energy = h[0] * inv2n2;
   out->enstrophy = h[1] * inv2n2;
   out->psi = (h[2] / h[3] - two_over_pi) / (1.0 - two_over_pi);
+  out->max_div = h[6] > 0.0 ? h[5] / h[6] : 0.0;
   out->mean_vx = vm[0] / d->n;
   out->mean_vy = vm[1] / d->n;
   out->step = d->steps;

@@ -1,24 +1,28 @@
 // ttsh_kernels.cuh - sm_103a kernels of the confined TTSH solver (templated on precision T
 // and grid size N).
 //
-// One step of Algorithm 1 (Appendix D) is two fused kernels:
+// One step of the integrating-factor Euler scheme of Appendix D (Algorithm 1) is two fused
+// kernels:
 //
 //   row pass  (one block per R rows of the N x N box, real space)
 //     inverse row transforms of omega^, v^x, v^y (column-transformed by the previous column
-//     pass), giving omega, v_x, v_y (the ENSURE'd v); then, per point,
+//     pass), giving omega, v_x, v_y in real space; then, per point,
 //       F0 = c1 v_x + lambda v_y omega,  F1 = c1 v_y - lambda v_x omega,  F2 = -gamma_w K omega
 //     with c1 = -b |v|^2 - gamma_v K, and forward row transforms of F0..F2, keeping only the
 //     columns mx <= N/4 that the 1/2 rule can keep.
 //
 //   column pass (one block per stored column mx = 0..N/4, Fourier space)
-//     forward column transforms of F0..F2; curl assembly rhs^ = i(kx F^1 - ky F^0) + F^2
-//     (line 3); integrating-factor Euler update (line 4); k = 0: omega^ = 0 and
-//     v^(0) <- exp((a-1) dt)(v^(0) + dt R^1(0)) with R^1(0) = F^(0) (lines 6-8, Eq. avg);
-//     zero |m|^2 > (N/4)^2 (lines 9-11); Hermitian average (line 13, only the mx = 0 column
-//     needs it in half-spectrum storage); then psi^ = omega^/k^2 and v^ = (i ky psi^,
-//     -i kx psi^) (lines 14-15) and the inverse column transforms of omega^, v^x, v^y.
+//     forward column transforms of F0..F2; curl of the non-linear terms of Eq. (mod2),
+//     rhs^ = i(kx F^1 - ky F^0) + F^2; integrating-factor Euler update
+//     omega^ <- exp((a - (1 - k^2)^2) dt)(omega^ + dt rhs^); k = 0: omega^ = 0 and the mean
+//     flow of Eq. (avg), v^(0) <- exp((a-1) dt)(v^(0) + dt R^1(0)) with R^1(0) = F^(0);
+//     zero |m|^2 > (N/4)^2 (1/2 rule); Hermitian average (only the mx = 0 column needs it in
+//     half-spectrum storage); then the stream function psi^ = omega^/k^2 and
+//     v^ = (i ky psi^, -i kx psi^), and the inverse column transforms of omega^, v^x, v^y.
 //
-// Why this equals lines 1-3: the advection term is taken in conservative form,
+// Why this equals the non-linear terms of Eq. (mod2) as Appendix D writes them (velocity
+// terms and v.grad(omega) in real space, then the curl): the advection term is taken in
+// conservative form,
 // v.grad(omega) = div(v omega), so i(kx F^1 - ky F^0) + F^2 = i(kx R^1y - ky R^1x)
 // - lambda (i kx DFT[v_x omega] + i ky DFT[v_y omega]) - gamma_w DFT[K omega] = rhs^.  The two
 // forms agree exactly (up to rounding) on every mode the update keeps: v and omega are
@@ -73,6 +77,7 @@ struct Args {
   double* rec;          // per-block time-series partials of a recorded step, or null
   RecCtl* recctl;       // with rec: where the column pass appends the step's sample
   int* err;             // device status word: 1 = a bounded wait in a kernel ran out
+  double* aux;          // two doubles: max |k.v^| and max |k||v^| of a divergence check
   int tma;              // 1: the row pass loads its G tile with the tensor-memory accelerator
   T a, b, lam, gv, gw, dt, dk, mean_decay;   // mean_decay = exp((a - 1) dt)
   double dx, cx, cy;    // grid spacing and the psi centre
@@ -80,7 +85,7 @@ struct Args {
 
 enum RowKind { ROW_STEP = 0, ROW_FWD_VEL = 1, ROW_FWD_MASK = 2, ROW_INV_FIELDS = 3,
                ROW_INV_MASK = 4, ROW_INV_DIAG = 5 };
-enum ColMode { COL_STEP = 0, COL_PROLOGUE = 1, COL_PROJECT = 2, COL_MASK = 3, COL_ADDW = 4 };
+enum ColMode { COL_STEP = 0, COL_PROLOGUE = 1, COL_PROJECT = 2, COL_MASK = 3, COL_ADDW = 4, COL_DIV = 5 };
 
 constexpr int kDiagQ = 5;   // per-block partials: sum|v|^2, sum w^2, sum|e_th.v|, sum|v|, #nonfinite
 constexpr int kSmemLimit = 220 * 1024;
@@ -93,8 +98,9 @@ template <int KIND> __host__ __device__ constexpr int row_inv_fields() {
   return KIND == ROW_STEP ? 3 : KIND == ROW_INV_FIELDS ? 3 : KIND == ROW_INV_DIAG ? 3
        : KIND == ROW_INV_MASK ? 1 : 0;
 }
+// (the diagnostic pass also forward-transforms v_x, v_y for the divergence check)
 template <int KIND> __host__ __device__ constexpr int row_fwd_fields() {
-  return KIND == ROW_STEP ? 3 : KIND == ROW_FWD_VEL ? 2 : KIND == ROW_FWD_MASK ? 1 : 0;
+  return KIND == ROW_STEP ? 3 : KIND == ROW_FWD_VEL ? 2 : KIND == ROW_FWD_MASK ? 1 : KIND == ROW_INV_DIAG ? 2 : 0;
 }
 
 // Default tile shapes (the autotuner may pick others for the step kernels).
@@ -186,13 +192,14 @@ struct ColGeo {
   static constexpr int PS = ilog2(PE);
   static constexpr int LP = padded_len<N, PS>();
   static constexpr int TT = N / PE;
-  static constexpr int NF = MODE == COL_STEP ? 3 : MODE == COL_PROJECT ? 2 : (MODE == COL_MASK || MODE == COL_ADDW) ? 1 : 0;
-  static constexpr int NI = MODE == COL_MASK ? 1 : 3;
+  static constexpr int NF = MODE == COL_STEP ? 3 : (MODE == COL_PROJECT || MODE == COL_DIV) ? 2
+                         : (MODE == COL_MASK || MODE == COL_ADDW) ? 1 : 0;
+  static constexpr int NI = MODE == COL_MASK ? 1 : MODE == COL_DIV ? 0 : 3;
   static constexpr int CB = (int)sizeof(cplx<T>);
   static constexpr int TW_BYTES = align16(TwTab<T, N>::ENTRIES * CB) + StageTab<T, N, PE>::BYTES;
   static constexpr int OFF_STAB = align16(TwTab<T, N>::ENTRIES * CB);
   static constexpr int ACC_BYTES = align16(NK * CB);
-  static constexpr int WS_BYTES = (MODE == COL_STEP || MODE == COL_ADDW) ? align16(NK * CB) : 0;
+  static constexpr int WS_BYTES = (MODE == COL_STEP || MODE == COL_ADDW || MODE == COL_DIV) ? align16(NK * CB) : 0;
   static constexpr int FIXED = TW_BYTES + ACC_BYTES + WS_BYTES + 64;
   static constexpr int FB0 = cmax(NF, NI) >= 4 ? 4 : cmax(NF, NI);
   static constexpr int FB = (FIXED + FB0 * LP * CB <= kSmemLimit) ? FB0
@@ -478,6 +485,7 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
   };
 
   cplx<T>* fw = sm;   // buffers of the forward transforms
+  if constexpr (KIND == ROW_INV_DIAG) fw = sm + R * LP;   // v_x, v_y (fields 1 and 2)
   if constexpr (KIND == ROW_STEP && Geo::SEPARATE) {
     if (A.rec != nullptr) record_partials<T, N, R, NT>(A, blk, y0, rl);
     fw = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_FWD);
@@ -511,8 +519,8 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
       // explicit fused multiply-adds: every kernel instantiation (single and batched) rounds
       // the same way
       const T v2 = fma(vx, vx, vy * vy);
-      const T c1 = fma(-A.b, v2, -(A.gv * Kv));        // line 1: rhs1 = c1 v
-      const T lw = A.lam * w;                           // line 2's advection, conservative form
+      const T c1 = fma(-A.b, v2, -(A.gv * Kv));        // velocity terms: -b|v|^2 v - gamma_v K v = c1 v
+      const T lw = A.lam * w;                           // advection, conservative form
       rl(0, r, x) = fma(c1, vx, lw * vy);
       rl(1, r, x) = fma(c1, vy, -(lw * vx));
       rl(2, r, x) = -(A.gw * Kv) * w;
@@ -567,7 +575,7 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
 
   // ---- forward row transforms (R2C), keep mx <= N/4 ----
   if constexpr (FF > 0) {
-    if constexpr (!Geo::SEPARATE) fft_batch<T, L, PE, -1, NT, N, LP>(sm, FF * R, tw, stab);
+    if constexpr (!Geo::SEPARATE) fft_batch<T, L, PE, -1, NT, N, LP>(fw, FF * R, tw, stab);
     // clusters: every block is past its inverse loads, so the shares can take the results
     if constexpr (CL > 1) cluster_sync();
     for (int e = tid; e < FF * R * H; e += NT) {
@@ -683,11 +691,17 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
         const int idx = ky & (N - 1);
         const T kyp = A.dk * (T)ky;
         cplx<T> a = f0 == 0 ? mk<T>(0, 0) : acc[j];
+        T q2 = (T)0;   // COL_DIV: |v^x|^2 + |v^y|^2
+        if constexpr (MODE == COL_DIV) q2 = f0 == 0 ? (T)0 : ws[j].x;
         for (int b = 0; b < nb; ++b) {
           const int f = f0 + b;
           const cplx<T> v = buf[b * LP + padi<PS>(idx)];
           if constexpr (MODE == COL_MASK || MODE == COL_ADDW) {
             a = v;
+          } else if constexpr (MODE == COL_DIV) {
+            // f = 0: v^x -> kx; f = 1: v^y -> ky (k . v^)
+            a = a + v * (f == 0 ? kxp : kyp);
+            q2 += v.x * v.x + v.y * v.y;
           } else {
             // f = 0: (F0 | v_x) -> -i ky; f = 1: (F1 | v_y) -> +i kx; f = 2: F2 -> 1
             if (f == 0) a = a - mul_i(v) * kyp;
@@ -697,11 +711,37 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
           }
         }
         acc[j] = a;
+        if constexpr (MODE == COL_DIV) ws[j].x = q2;
       }
       __syncthreads();   // buf is refilled by the next batch
     }
 
-    // ---- update (Algorithm 1 lines 3-11) ----
+    if constexpr (MODE == COL_DIV) {
+      // largest |k.v^| and |k||v^| over the stored modes of the 1/2-rule disc, in double;
+      // maxima of non-negative doubles combine as their bit patterns (order-independent)
+      double dmax = 0.0, kvmax = 0.0;
+      for (int j = tid; j < NK; j += NT) {
+        const int ky = ky_of(j);
+        const int m2 = kx * kx + ky * ky;
+        if (m2 > M * M) continue;
+        const double ax = (double)acc[j].x, ay = (double)acc[j].y;
+        const double dkd = (double)A.dk;
+        dmax = fmax(dmax, sqrt(ax * ax + ay * ay));
+        kvmax = fmax(kvmax, dkd * sqrt((double)m2) * sqrt((double)ws[j].x));
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        dmax = fmax(dmax, __shfl_down_sync(0xffffffffu, dmax, off));
+        kvmax = fmax(kvmax, __shfl_down_sync(0xffffffffu, kvmax, off));
+      }
+      if ((tid & 31) == 0) {
+        atomicMax(reinterpret_cast<unsigned long long*>(A.aux), (unsigned long long)__double_as_longlong(dmax));
+        atomicMax(reinterpret_cast<unsigned long long*>(A.aux) + 1, (unsigned long long)__double_as_longlong(kvmax));
+      }
+      return;
+    }
+
+    // ---- update: integrating-factor Euler, k = 0, 1/2 rule ----
     for (int j = tid; j < NK; j += NT) {
       const int ky = ky_of(j);
       const int m2 = kx * kx + ky * ky;
@@ -732,7 +772,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
         for (int c = 0; c < 2; ++c) {
           T vm;
           if constexpr (MODE == COL_STEP)
-            vm = A.mean_decay * (A.vmean[c] + A.dt * (s0[c] * invN));   // line 8
+            vm = A.mean_decay * (A.vmean[c] + A.dt * (s0[c] * invN));   // Eq. (avg)
           else
             vm = s0[c] * invN;                                              // DFT[v](0)
           s0[2 + c] = vm;
@@ -742,7 +782,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
     }
     __syncthreads();
     if constexpr (MODE == COL_STEP || MODE == COL_PROJECT || MODE == COL_ADDW) {
-      // line 13: Hermitian average; with half-spectrum storage only mx = 0 pairs are stored
+      // Hermitian average; with half-spectrum storage only mx = 0 pairs are stored
       if (kx == 0) {
         for (int ky = 1 + tid; ky <= M; ky += NT) {
           const cplx<T> p = acc[ky], q = acc[NK - ky];
@@ -791,7 +831,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
           const T k2 = A.dk * A.dk * (T)m2;
           const T inv = m2 > 0 ? invN / k2 : (T)0;
           if (f == 0) v = w * invN;                       // omega
-          else if (f == 1) v = mul_i(w) * (kyp * inv);    // v^x = i ky psi^   (line 15)
+          else if (f == 1) v = mul_i(w) * (kyp * inv);    // v^x = i ky psi^   (stream function)
           else v = mul_i(w) * (-kxp * inv);               // v^y = -i kx psi^
           if (m2 == 0 && f >= 1) v = mk<T>(s0[2 + (f - 1)] * invN, (T)0);   // mean flow
         }

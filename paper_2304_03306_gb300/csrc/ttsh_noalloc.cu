@@ -15,7 +15,14 @@
 // time) race on it and must be serialised by the caller.  Nothing in it has to start at
 // zero: each call first rebuilds the whole inverse-transformed buffer from the caller's
 // state, and every element a pass reads was written earlier in the same call; the twiddle
-// tables are written once per device.
+// tables are written once per device, and that first call waits until they are on the
+// device.
+//
+// Every wait inside the kernels is bounded (the column pass's bulk-copy completion), but
+// this entry point has no status word to report a wait that ran out: the domain path
+// reports it as TTSH_E_TIMEOUT at its next synchronising call, here the step simply goes on
+// (the state of that call is then not valid).  No such wait has ever run out; callers that
+// need the report use the domain path.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -83,6 +90,10 @@ ttsh_status setup_device(int dev, char** out) {
   char* base = static_cast<char*>(p);
   e = cudaMemcpy(base + kTwF32Off, g_tw_host_f32, kTwF32Bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(base + kTwF64Off, g_tw_host_f64, kTwF64Bytes, cudaMemcpyHostToDevice);
+  // A copy from pageable host memory may return before it has reached the device, and a
+  // non-blocking caller stream does not wait for the legacy stream the copies ran on: wait
+  // for them here, before any kernel on the caller's stream can read the tables.
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_bad(e, "twiddle upload to the no-allocation scratch");
   g_scratch_ptr[dev] = base;
   *out = base;

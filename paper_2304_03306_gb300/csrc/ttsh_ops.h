@@ -13,14 +13,15 @@ struct DomainDev {
   void* what;      // omega^ half-spectrum, H x NK complex
   void* vmean;     // v^(0), 2 reals
   void* K;         // processed mask, N x N reals
-  void* G;         // [4][H][N] complex
+  void* G;         // [3][H][N] complex
   void* Rr;        // [3][H][N] complex
   void* tw;        // N complex twiddles W_N^m
   double* real;    // [3][N][N] double staging
   double* part;    // row-block diagnostic partials
   double* colhist; // H x (N/4 + 1) spectrum partials
   int* bad;        // non-finite counter
-  double* out;     // reduced diagnostics (8 doubles) + spectrum bins
+  double* out;     // reduced diagnostics (8 doubles: 5 sums, 2 divergence maxima, 1 spare) + spectrum bins
+  unsigned char* knaive;   // binary mask K_naive as given (1 = masked), N x N bytes
   double* rec;     // time-series partials of a recorded step (null: plain step)
   void* recctl;    // time-series write position (RecCtl), used with rec
   double a, b, lam, gv, gw, dx, dt;
@@ -37,7 +38,7 @@ struct DomainDev {
 
 enum { K_ROW_STEP = 0, K_ROW_FWD_VEL = 1, K_ROW_FWD_MASK = 2, K_ROW_INV_FIELDS = 3,
        K_ROW_INV_MASK = 4, K_ROW_INV_DIAG = 5 };
-enum { K_COL_STEP = 0, K_COL_PROLOGUE = 1, K_COL_PROJECT = 2, K_COL_MASK = 3, K_COL_ADDW = 4 };
+enum { K_COL_STEP = 0, K_COL_PROLOGUE = 1, K_COL_PROJECT = 2, K_COL_MASK = 3, K_COL_ADDW = 4, K_COL_DIV = 5 };
 
 using RowFn = cudaError_t (*)(int kind, const DomainDev&, cudaStream_t);
 using ColFn = cudaError_t (*)(int mode, const DomainDev&, cudaStream_t);

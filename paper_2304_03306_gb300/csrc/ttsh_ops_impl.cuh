@@ -25,6 +25,7 @@ static Args<T> make_args(const DomainDev& d) {
   a.rec = d.rec;
   a.recctl = static_cast<RecCtl*>(d.recctl);
   a.err = d.err;
+  a.aux = d.out ? d.out + 5 : nullptr;
   a.tma = 0;
   const double dk = 2.0 * 3.14159265358979323846264338327950288 / ((double)d.n * d.dx);
   a.a = (T)d.a;
@@ -142,6 +143,7 @@ static cudaError_t launch_col(int mode, const DomainDev& d, cudaStream_t s) {
     case K_COL_PROJECT: return launch_col_mode<T, N, COL_PROJECT>(d, s);
     case K_COL_MASK: return launch_col_mode<T, N, COL_MASK>(d, s);
     case K_COL_ADDW: return launch_col_mode<T, N, COL_ADDW>(d, s);
+    case K_COL_DIV: return launch_col_mode<T, N, COL_DIV>(d, s);
   }
   return cudaErrorInvalidValue;
 }

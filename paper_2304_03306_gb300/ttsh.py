@@ -37,7 +37,7 @@ class ttsh_params(ctypes.Structure):
 
 class ttsh_diag(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("enstrophy", ctypes.c_double),
-                ("psi", ctypes.c_double), ("mean_vx", ctypes.c_double),
+                ("psi", ctypes.c_double), ("max_div", ctypes.c_double), ("mean_vx", ctypes.c_double),
                 ("mean_vy", ctypes.c_double), ("step", ctypes.c_int64),
                 ("nonfinite", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
@@ -69,6 +69,7 @@ def load_library(path: str = LIB_PATH):
         "ttsh_set_stream": (ctypes.c_int, [_P, _P]),
         "ttsh_set_velocity": (ctypes.c_int, [_P, _D, _D]),
         "ttsh_set_velocity_device": (ctypes.c_int, [_P, _P, _P]),
+        "ttsh_init_noise": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double]),
         "ttsh_step": (ctypes.c_int, [_P, ctypes.c_int64]),
         "ttsh_step_record": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P, ctypes.c_int64, _D]),
         "ttsh_get_fields": (ctypes.c_int, [_P, _D, _D, _D]),
@@ -113,6 +114,7 @@ def load_library(path: str = LIB_PATH):
         "ttsh_lyap_directions": (ctypes.c_int, [_P, _D]),
         "ttsh_lyap_destroy": (None, [_P]),
         "ttsh_step_count": (ctypes.c_int64, [_P]),
+        "ttsh_fma_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _D]),
         "ttsh_step_noalloc": (ctypes.c_int, [ctypes.POINTER(ttsh_params), _P, _P, _P, ctypes.c_int64, _P]),
         "ttsh_last_error": (ctypes.c_char_p, []),
     }
@@ -189,6 +191,10 @@ def ttsh_set_velocity(h, vx, vy, n: int):
 
 def ttsh_set_velocity_device(h, vx_ptr: int, vy_ptr: int):
     _check(load_library().ttsh_set_velocity_device(h, vx_ptr, vy_ptr))
+
+
+def ttsh_init_noise(h, seed: int, amplitude: float):
+    _check(load_library().ttsh_init_noise(h, int(seed), float(amplitude)))
 
 
 def ttsh_step(h, nsteps: int):
@@ -468,6 +474,9 @@ class Domain:
     def set_velocity(self, vx, vy):
         ttsh_set_velocity(self.h, vx, vy, self.n)
 
+    def init_noise(self, seed: int, amplitude: float = 0.01):
+        ttsh_init_noise(self.h, seed, amplitude)
+
     def set_velocity_device(self, vx_ptr: int, vy_ptr: int):
         ttsh_set_velocity_device(self.h, vx_ptr, vy_ptr)
 
@@ -585,3 +594,10 @@ class Lyapunov:
             self.close()
         except Exception:
             pass
+
+
+def ttsh_fma_peak(precision: int, iters: int) -> float:
+    """Measured fused multiply-add throughput of the current GPU in TFLOP/s."""
+    out = ctypes.c_double()
+    _check(load_library().ttsh_fma_peak(int(precision), int(iters), ctypes.byref(out)))
+    return out.value

@@ -41,3 +41,11 @@ def test_plan_variant_keys_match_the_record_layout():
         assert kernel in ("row_pass", "col_pass") and int(n) > 0 and prec in ("32", "64")
         for e in entries:
             assert e["dram_bytes_per_launch"] > 0 and len(e["variant"]) in ((1,) if kernel == "col_pass" else (2, 3))
+
+
+def test_oracle_replicas_time_every_process():
+    """The all-core CPU baseline: independent oracle processes (spawned), each timed over its
+    own copy of the workload; the aggregate is the sum of their rates."""
+    rate, P, steps, wall = bench.oracle_replicas("circle64_fp64", 10, procs=2, warm_steps=1, timed_steps=5)
+    assert P == 2 and steps == [5, 5] and wall > 0
+    assert rate > 0

@@ -52,6 +52,9 @@ def rel(a, b):
 
 
 CFG = dict(n=32, width=32, modes=4, layers=2, max_batch=2)
+# the corrector's configured size: 256^2 coarse grid, width 32, 16 modes, 4 layers
+CFG_FULL = dict(n=256, width=32, modes=16, layers=4, max_batch=2)
+SIZES = [pytest.param(CFG, id="n32-m4-l2"), pytest.param(CFG_FULL, id="n256-m16-l4")]
 
 
 def make(T, seed=0, **kw):
@@ -66,8 +69,9 @@ def test_param_count_matches_oracle_layout(T):
     assert net.nparams == F.num_params(cfg)
 
 
-def test_forward_matches_oracle(T, torch):
-    net, cfg = make(T, seed=3)
+@pytest.mark.parametrize("size", SIZES)
+def test_forward_matches_oracle(T, torch, size):
+    net, cfg = make(T, seed=3, **size)
     rng = np.random.default_rng(0)
     x = rng.standard_normal((2, cfg.n, cfg.n, 4)).astype(np.float32)
     xd = torch.tensor(x, device="cuda")
@@ -79,8 +83,9 @@ def test_forward_matches_oracle(T, torch):
     assert rel(yd.cpu().numpy(), ref) <= TOL
 
 
-def test_gradients_match_oracle_block_by_block(T, torch):
-    net, cfg = make(T, seed=5)
+@pytest.mark.parametrize("size", SIZES)
+def test_gradients_match_oracle_block_by_block(T, torch, size):
+    net, cfg = make(T, seed=5, **size)
     rng = np.random.default_rng(1)
     x = rng.standard_normal((2, cfg.n, cfg.n, 4)).astype(np.float32)
     t = rng.standard_normal((2, cfg.n, cfg.n)).astype(np.float32)

@@ -165,6 +165,85 @@ def test_2048_few_steps(T, prec):
     check_fields(dom, s, TOL[prec])
 
 
+def threaded_oracle_run(s, K, p, steps):
+    """The oracle with its transforms on all host cores (the same unitary DFT pair)."""
+    dft, idft = O.threaded_dft()
+    return O.run(s, K, p, steps, dft=dft, idft=idft)
+
+
+_LARGE_REF = {}
+
+
+def large_reference(n, dx, R, seed, steps):
+    """Oracle state after `steps` steps from the seeded noise (amplitude 0.3), cached per case."""
+    key = (n, dx, R, seed, steps)
+    if key not in _LARGE_REF:
+        mask = ti.circle_mask(n, dx, R)
+        p = O.Params(n=n, dx=dx)
+        vx, vy = ti.noise_velocity(mask, seed, 0.3)
+        dft, idft = O.threaded_dft()
+        K = O.process_mask(mask, dft=dft, idft=idft)
+        s = O.project_velocity(vx, vy, p, dft=dft, idft=idft)
+        _LARGE_REF.clear()
+        _LARGE_REF[key] = (mask, vx, vy, threaded_oracle_run(s, K, p, steps))
+    return _LARGE_REF[key]
+
+
+@pytest.mark.parametrize("prec,n,dx,steps", [(32, 4096, 0.01, 2), (64, 4096, 0.01, 2), (32, 8192, 0.005, 1)])
+def test_dense_turbulent_state_at_full_size(T, prec, n, dx, steps):
+    """A dense noise state (amplitude 0.3) of the turbulent circle, R = 12, on the 4096^2 grid
+    and the paper's 8192^2 grid, with the default (autotuner's first) row and column plans
+    of those sizes - at 8192^2 the clustered row pass and the column pass that holds two of
+    its three fields at a time - against the oracle element by element."""
+    mask, vx, vy, ref = large_reference(n, dx, 12.0, 4, steps)
+    dom = T.Domain(mask, n, dx, precision=prec)
+    dom.set_velocity(vx, vy)
+    dom.step(steps)
+    gvx, gvy, gw = dom.fields()
+    dom.close()
+    assert rel(gw, O.vorticity(ref)) <= TOL[prec]
+    assert rel(np.stack([gvx, gvy]), np.stack([ref.vx, ref.vy])) <= TOL[prec]
+
+
+# --------------------------------------------------------- device initial state
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("n,dx,shape,seed", [(64, 0.25, "circle", 1), (256, 0.08, "dumbbell", 7),
+                                             (512, 0.04, "circle", 2**64 - 12345)])
+def test_init_noise_equals_the_host_generator_bit_for_bit(T, prec, n, dx, shape, seed):
+    """ttsh_init_noise draws the random initial state on the device; projected, it gives the
+    same state bits as the host generator's field passed through ttsh_set_velocity (the
+    counter-based SplitMix64 definition, including a seed above 2^63)."""
+    mask = ti.circle_mask(n, dx, 5.4) if shape == "circle" else ti.dumbbell_mask(n, dx, 3.0, 4.5)
+    a = T.Domain(mask, n, dx, precision=prec)
+    a.init_noise(seed, 0.01)
+    b = T.Domain(mask, n, dx, precision=prec)
+    b.set_velocity(*ti.noise_velocity(mask, seed, 0.01))
+    wa, va = a.spectral_state()
+    wb, vb = b.spectral_state()
+    assert np.array_equal(wa, wb) and np.array_equal(va, vb)
+    assert np.abs(wa).max() > 0
+    assert a.steps == 0
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_init_noise_then_100_steps_match_oracle(T, prec):
+    """The timed workload's initial state made on the device, then 100 steps, against the
+    oracle started from the host generator's field."""
+    w = ti.WORKLOADS["circle512"]
+    n, dx = w["n"], w["dx"]
+    mask = ti.circle_mask(n, dx, w["radius"])
+    dom = T.Domain(mask, n, dx, precision=prec)
+    dom.init_noise(w["seed"], 0.01)
+    dom.step(100)
+    p = O.Params(n=n, dx=dx)
+    s = O.run(O.project_velocity(*ti.noise_velocity(mask, w["seed"], 0.01), p), O.process_mask(mask), p, 100)
+    check_fields(dom, s, TOL[prec])
+    dom.close()
+
+
 # --------------------------------------------------------- closed forms at any size
 
 @pytest.mark.parametrize("prec,n", [(32, 16), (32, 8192), (64, 16), (64, 4096), (32, 1024)])
@@ -299,6 +378,35 @@ def test_invariants_of_gpu_state(T, prec):
 
 
 # ------------------------------------------------------------------ diagnostics
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_max_div_reports_incompressibility_and_leaves_stepping_unchanged(T, prec):
+    """ttsh_diag.max_div: max |k.v^| / max |k||v^| of the real-space velocity (P4, div v = 0
+    by the stream-function construction) is at round-off level; the float transforms always
+    leave some.  Taking diagnostics between steps does not change the trajectory."""
+    n, dx = 128, 0.16
+    dom, p, K, s = setup(T, n, dx, 5.3, prec, 5, amp=0.3)
+    ref, _, _, _ = setup(T, n, dx, 5.3, prec, 5, amp=0.3)
+    dom.step(20)
+    d = dom.diagnostics()
+    assert 0.0 <= d["max_div"] <= (1e-13 if prec == 64 else 1e-6)
+    if prec == 32:
+        assert d["max_div"] > 0.0
+    dom.step(20)
+    ref.step(40)
+    wa, va = dom.spectral_state()
+    wb, vb = ref.spectral_state()
+    assert np.array_equal(wa, wb) and np.array_equal(va, vb)
+
+
+def test_fma_peak_probe(T):
+    """The measured FMA throughputs the rooflines use are in the range GB300's unit counts
+    allow (FP32: 152 SMs x 128 lanes x 2 flops x <= 2.07 GHz = 80.5 TFLOP/s nominal; FP64 a
+    small fraction of that on this part)."""
+    f32 = T.ttsh_fma_peak(32, 1 << 16)
+    f64 = T.ttsh_fma_peak(64, 1 << 11)
+    assert 20.0 < f32 < 90.0
+    assert 0.05 < f64 < f32
 
 @pytest.mark.parametrize("prec", [64, 32])
 def test_diagnostics_match_oracle(T, prec):

@@ -102,7 +102,7 @@ def test_projection_reproduces_analytic_vorticity_and_velocity():
 @pytest.mark.parametrize("m", [(1, 0), (0, 1), (2, 3), (-3, 3), (4, -1), (8, 0), (5, 6)])
 def test_linear_single_mode_exact_growth(m):
     """b = lambda = 0, K = 0: each mode grows by exactly exp[(a - (1 - k^2)^2) dt] per step
-    (Algorithm 1 line 4 integrates the linear operator exactly)."""
+    (the integrating factor of Appendix D integrates the linear operator exactly)."""
     p = O.Params(n=32, dx=0.25, b=0.0, lam=0.0)
     amp = 0.3
     vx, vy, w, (kx, ky) = stream_mode(p, m, amp)
@@ -488,3 +488,19 @@ def test_dumbbell_region_is_closed_and_excludes_outside_peaks():
     psi2, a, b = O.dumbbell_order_parameter(w, p, [(-2.0, 0.0), (2.0, 0.0)], 1.5)
     assert (a, b) == (5.0, -0.5)
     assert psi2 == pytest.approx(4.5 / 5.5, abs=1e-15)
+
+
+def test_threaded_transforms_equal_the_default_ones():
+    """The all-core transform pair used for large-grid tests is the same unitary DFT."""
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal((64, 64))
+    dft, idft = O.threaded_dft(2)
+    np.testing.assert_allclose(dft(f), O.dft2(f), atol=1e-13)
+    np.testing.assert_allclose(idft(O.dft2(f)), f, atol=1e-13)
+    p = O.Params(n=32, dx=0.5)
+    mask = ti.circle_mask(32, 0.5, 5.2)
+    s = O.project_velocity(*ti.noise_velocity(mask, 3, 0.3), p)
+    K = O.process_mask(mask)
+    a = O.step(s, K, p)
+    b = O.step(s, K, p, dft=dft, idft=idft)
+    np.testing.assert_allclose(O.vorticity(b), O.vorticity(a), atol=1e-14)
