@@ -394,13 +394,25 @@ def run_ours(args, rank, world, local_rank):
             objs.append(o)
         bt = ttsh.Batch(objs, stream=stream.cuda_stream)
         Sb = max(32, S // 20)
+        persistent = bt.persistent
+        grouped_ms = None
+        if persistent:   # the grouped launches (one per pass per group of equal domains), for comparison
+            bt.set_persistent(False)
+            bt.step(Sb)
+            bt.synchronize()
+            grouped_ms = 1e3 * max_over_ranks(timed_segments(bt, K, Sb, record=False)) / (Sb * K)
+            bt.set_persistent(True)
         bt.step(Sb)
         bt.synchronize()
         barrier()
         tb = max_over_ranks(timed_segments(bt, K, Sb, record=False))
         pts = sum(dspec["n"] ** 2 for dspec in sweep)
         batched = {"value": pts * Sb * K / tb, "unit": UNIT, "domains": len(sweep),
+                   "grouped_value": pts / (grouped_ms * 1e-3) if grouped_ms else None,
                    "grid_points": pts, "solver_steps_per_step": Sb, "launch_groups": bt.groups,
+                   "persistent": persistent,
+                   "launches_per_call": 1 if persistent else 2 * bt.groups * Sb,
+                   "grouped_ms_per_solver_step": grouped_ms,
                    "scaling": "strong (the 48 domains are split across the ranks)",
                    "ms_per_solver_step": 1e3 * tb / (Sb * K),
                    "workload": "24 circles (R 5.0-8.0, forward and backward members) + 24 dumbbells "

@@ -308,6 +308,19 @@ ttsh_status ttsh_batch_create(ttsh_domain* const* domains, int32_t ndom, void* s
 ttsh_status ttsh_batch_step(ttsh_batch* b, int64_t nsteps);
 ttsh_status ttsh_batch_synchronize(ttsh_batch* b);
 int32_t ttsh_batch_groups(const ttsh_batch* b);   /* number of launch groups, -1 if NULL */
+
+/* Persistent stepping of a batch (the default where the batch allows it): one kernel launch
+ * per ttsh_batch_step call advances every domain by all nsteps steps.  The launch keeps as
+ * many blocks resident as the GPU holds; they take work items - one row-pass or column-pass
+ * block of one domain's step - in order from a counter, and each item waits (bounded, 2 s,
+ * TTSH_E_TIMEOUT on the domain otherwise) only for the previous pass of its own domain, so
+ * domains of different sizes proceed independently without a grid-wide barrier.  Needs
+ * every domain in one precision, n <= 512 and the default tile shapes (plan variants 0);
+ * each domain's result is bit-identical to ttsh_step.  on = 1 selects it (TTSH_E_UNSUPPORTED
+ * if the batch does not allow it), 0 the grouped launches described above.
+ * ttsh_batch_persistent returns 1, 0, or -1 for NULL. */
+ttsh_status ttsh_batch_set_persistent(ttsh_batch* b, int32_t on);
+int32_t ttsh_batch_persistent(const ttsh_batch* b);
 void ttsh_batch_destroy(ttsh_batch* b);           /* NULL is a no-op; domains are untouched */
 
 /* Temporal power spectral density of the vorticity, Eq. (PSD) of Sec. III.B:

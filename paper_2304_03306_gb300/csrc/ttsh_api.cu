@@ -714,6 +714,15 @@ struct ttsh_batch {
   int graph_len = 0;
   cudaGraphExec_t tail = nullptr;    // the last call's remainder (tail_len < kBatchGraphLen steps)
   int tail_len = 0;
+  // persistent mode: one launch per ttsh_batch_step call for every domain (one precision,
+  // n <= max_n, default tile shapes); see ttsh_persist.cuh
+  bool can_persist = false;
+  bool persistent = false;
+  ttsh::PersistOps pops{};
+  void* pdoms = nullptr;               // device domain table
+  void* pitems = nullptr;              // device work-item list of one step
+  unsigned long long* pctl = nullptr;  // device control block: 2 + 2 ndom counters
+  int pips = 0, pgrid = 0;
 };
 
 namespace {
@@ -1375,6 +1384,63 @@ ttsh_status ttsh_batch_create(ttsh_domain* const* domains, int32_t ndom, void* s
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->order, cudaEventDisableTiming);
   if (e != cudaSuccess) return cleanup(cuda_fail(e, "batch streams"));
+  // persistent mode where the batch allows it (the default then)
+  {
+    const int prec = b->all[0]->p.precision;
+    bool ok = prec == 32 ? ttsh::persist_f32(&b->pops) : ttsh::persist_f64(&b->pops);
+    for (ttsh_domain* d : b->all)
+      ok = ok && d->p.precision == prec && d->n <= b->pops.max_n && b->pops.row_blocks(d->n) > 0 &&
+           d->rv == 0 && d->cv == 0;
+    if (ok) {
+      const int nd = (int)b->all.size();
+      std::vector<unsigned char> dt((size_t)b->pops.domain_bytes * nd);
+      for (int k = 0; k < nd; ++k)
+        b->pops.pack(b->all[k]->dev, b->pops.row_blocks(b->all[k]->n), b->all[k]->H,
+                     dt.data() + (size_t)k * b->pops.domain_bytes);
+      // one step's items: the domains in kGroups groups of about equal work (larger domains
+      // first, each to the lightest group); the rows of every group, then the columns of
+      // every group in the same order, so each item's dependencies were taken kGroups - 1
+      // group-phases earlier (measured on the 48-domain sweep: two groups 66-68 us per step,
+      // four groups 72 us)
+      constexpr int kGroups = 2;
+      std::vector<int> order(nd);
+      for (int k = 0; k < nd; ++k) order[k] = k;
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->all[x]->n > b->all[y]->n; });
+      std::vector<int> grp[kGroups];
+      long long load[kGroups] = {};
+      for (int k : order) {
+        int w = 0;
+        for (int gi = 1; gi < kGroups; ++gi)
+          if (load[gi] < load[w]) w = gi;
+        grp[w].push_back(k);
+        load[w] += (long long)b->all[k]->n * b->all[k]->n;
+      }
+      std::vector<int> items;
+      for (int phase = 0; phase < 2; ++phase)
+        for (int gi = 0; gi < kGroups; ++gi)
+          for (int k : grp[gi]) {
+            const int nb = phase == 0 ? b->pops.row_blocks(b->all[k]->n) : b->all[k]->H;
+            for (int blk = 0; blk < nb; ++blk) {
+              items.push_back(k);
+              items.push_back(phase);
+              items.push_back(blk);
+              items.push_back(0);
+            }
+          }
+      b->pips = (int)(items.size() / 4);
+      static_assert(sizeof(int) * 4 == 16, "work item layout");
+      cudaError_t pe = b->pops.item_bytes == 16 ? cudaSuccess : cudaErrorInvalidValue;
+      if (pe == cudaSuccess) pe = cudaMalloc(&b->pdoms, dt.size());
+      if (pe == cudaSuccess) pe = cudaMalloc(&b->pitems, items.size() * sizeof(int));
+      if (pe == cudaSuccess) pe = cudaMalloc(&b->pctl, (2 + 2 * (size_t)nd) * sizeof(unsigned long long));
+      if (pe == cudaSuccess) pe = cudaMemcpy(b->pdoms, dt.data(), dt.size(), cudaMemcpyHostToDevice);
+      if (pe == cudaSuccess) pe = cudaMemcpy(b->pitems, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice);
+      if (pe == cudaSuccess) pe = b->pops.prepare(&b->pgrid);
+      if (pe != cudaSuccess) return cleanup(cuda_fail(pe, "persistent batch set-up"));
+      b->can_persist = true;
+      b->persistent = true;
+    }
+  }
   for (auto& g : b->groups) {
     const int ab = g.doms[0]->ops.args_bytes;
     std::vector<unsigned char> host((size_t)ab * g.doms.size());
@@ -1403,6 +1469,16 @@ ttsh_status ttsh_batch_step(ttsh_batch* b, int64_t nsteps) {
     TTSH_CUDA(cudaStreamWaitEvent(b->stream, b->order, 0), "order wait");
   }
   ttsh_status st;
+  if (b->persistent) {
+    if (nsteps > 0) {
+      const size_t ctl_bytes = (2 + 2 * b->all.size()) * sizeof(unsigned long long);
+      TTSH_CUDA(cudaMemsetAsync(b->pctl, 0, ctl_bytes, b->stream), "persistent batch reset");
+      TTSH_CUDA(b->pops.launch(b->pdoms, b->pitems, b->pips, (long long)nsteps, b->pctl, b->pgrid, b->stream),
+                "persistent batch launch");
+    }
+    for (ttsh_domain* d : b->all) d->steps += nsteps;
+    return TTSH_OK;
+  }
   int64_t left = nsteps;
   if (left >= kBatchGraphLen && !b->graph) {
     if ((st = batch_build_graph(b, kBatchGraphLen, &b->graph)) != TTSH_OK) return st;
@@ -1436,6 +1512,18 @@ ttsh_status ttsh_batch_synchronize(ttsh_batch* b) {
 
 int32_t ttsh_batch_groups(const ttsh_batch* b) { return b ? (int32_t)b->groups.size() : -1; }
 
+ttsh_status ttsh_batch_set_persistent(ttsh_batch* b, int32_t on) {
+  if (!b) return fail(TTSH_E_INVALID, "batch is NULL");
+  if (on != 0 && on != 1) return fail(TTSH_E_INVALID, "on must be 0 or 1");
+  if (on && !b->can_persist)
+    return fail(TTSH_E_UNSUPPORTED,
+                "persistent stepping needs one precision, n <= 512 and the default tile shapes in every domain");
+  b->persistent = on == 1;
+  return TTSH_OK;
+}
+
+int32_t ttsh_batch_persistent(const ttsh_batch* b) { return b ? (b->persistent ? 1 : 0) : -1; }
+
 void ttsh_batch_destroy(ttsh_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -1445,6 +1533,9 @@ void ttsh_batch_destroy(ttsh_batch* b) {
     if (g.branch) cudaStreamDestroy(g.branch);
     if (g.join) cudaEventDestroy(g.join);
   }
+  if (b->pdoms) cudaFree(b->pdoms);
+  if (b->pitems) cudaFree(b->pitems);
+  if (b->pctl) cudaFree(b->pctl);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->order) cudaEventDestroy(b->order);
   if (b->capture) cudaStreamDestroy(b->capture);

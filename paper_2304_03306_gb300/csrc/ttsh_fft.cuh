@@ -218,6 +218,17 @@ struct StageTab {
   }
 };
 
+// Block barrier over the NT threads that run a pass body: a named hardware barrier (id 1)
+// with an explicit thread count, so a body may run in a block with more threads than it
+// uses (the persistent batched kernel: the threads beyond NT skip the body and wait at the
+// kernel's own barriers).  With NT = blockDim.x it is the same as a full block barrier.  NT must
+// be a multiple of the warp size.
+template <int NT>
+__device__ __forceinline__ void block_sync() {
+  static_assert(NT % 32 == 0, "a named barrier counts whole warps");
+  asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+
 // Barrier between the stages of one transform.  A transform is owned by TT = L/PE
 // consecutive threads; when TT divides 32 every transform lies inside one warp and touches
 // only its own buffer, so a warp barrier (which also orders the warp's shared-memory
@@ -233,7 +244,7 @@ __device__ __forceinline__ void stage_sync() {
       __syncwarp(wl == 32 ? 0xffffffffu : ((1u << wl) - 1u));
     }
   } else {
-    __syncthreads();
+    block_sync<NT>();
   }
 }
 
@@ -321,13 +332,13 @@ __device__ __forceinline__ void fft_batch(cplx<T>* sm, int B, const TwTab<T, TWN
   constexpr int PER = NT / TT;
   const int j = threadIdx.x % TT;
   const int slot = threadIdx.x / TT;
-  __syncthreads();
+  block_sync<NT>();
   for (int c0 = 0; c0 < B; c0 += PER) {
     const int b = c0 + slot;
     const bool active = b < B;
     stockham_all<T, L, PE, 1, DIR, PS, TWN, NT>(sm + (active ? b : 0) * LP, j, active, tw, stab, b, ld);
   }
-  if constexpr (TT <= 32 && 32 % TT == 0) __syncthreads();
+  if constexpr (TT <= 32 && 32 % TT == 0) block_sync<NT>();
 }
 
 }  // namespace ttsh

@@ -112,6 +112,15 @@ template <typename T, int N>
 __host__ __device__ constexpr int default_row_pe() { return sizeof(T) == 4 ? 16 : 8; }
 template <typename T, int N>
 __host__ __device__ constexpr int default_col_pe() { return sizeof(T) == 4 ? (N <= 1024 ? 8 : 16) : 8; }
+// Tile shape of the step kernels' first variant (the plan a domain starts with).  As the
+// defaults above, except the float 512^2 step, which starts with two rows per block and 16
+// points per thread in both passes: the shape whose blocks are small enough (96 threads,
+// < 45 KB of shared memory) for the persistent batched stepper to keep several resident per
+// SM; the autotuner may pick the faster single-domain shape.
+template <typename T, int N>
+__host__ __device__ constexpr int default_step_rows() { return sizeof(T) == 4 && N == 512 ? 2 : default_rows<T, N>(); }
+template <typename T, int N>
+__host__ __device__ constexpr int default_step_col_pe() { return sizeof(T) == 4 && N == 512 ? 16 : default_col_pe<T, N>(); }
 // blocks per cluster of the default step row pass (8192^2 float: one row per block, pairs)
 template <typename T, int N>
 __host__ __device__ constexpr int default_row_cluster() { return sizeof(T) == 4 && N >= 8192 ? 2 : 1; }
@@ -274,7 +283,7 @@ __device__ __forceinline__ void record_partials(const Args<T>& A, int blk, int y
     for (int k = 0; k < kDiagQ - 1; ++k) wsum[warp][k] = (double)q[k];
     wsum[warp][kDiagQ - 1] = (double)bad;
   }
-  __syncthreads();
+  block_sync<NT>();
   if (threadIdx.x < kDiagQ) {
     double t = 0.0;
     for (int w2 = 0; w2 < NW; ++w2) t += wsum[w2][threadIdx.x];
@@ -409,7 +418,7 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       }
-      __syncthreads();
+      block_sync<NT>();
       if (tid == 0) {
         constexpr unsigned bytes = (unsigned)(Geo::NPL * H * R * Geo::CB);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -434,7 +443,7 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
     }
   }
   cp_async_wait_all();   // tables and staged inputs
-  __syncthreads();
+  block_sync<NT>();
 
   if constexpr (CL > 1) cluster_sync();   // every block's share is staged and visible
 
@@ -564,11 +573,11 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
     // fixed-order block reduction (deterministic)
     double* red = reinterpret_cast<double*>(smem_raw + Geo::OFF_RED);
     for (int q = 0; q < kDiagQ; ++q) red[q * 1024 + tid] = acc[q];
-    __syncthreads();
+    block_sync<NT>();
     for (int s = 512; s >= 1; s >>= 1) {
       if (tid < s && tid + s < NT)
         for (int q = 0; q < kDiagQ; ++q) red[q * 1024 + tid] += red[q * 1024 + tid + s];
-      __syncthreads();
+      block_sync<NT>();
     }
     if (tid < kDiagQ) A.part[(size_t)blk * kDiagQ + tid] = red[tid * 1024];
   }
@@ -662,7 +671,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       }
-      __syncthreads();
+      block_sync<NT>();
       if (tid == 0) {
         constexpr unsigned bytes = (unsigned)(NF * N * CB);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
@@ -713,7 +722,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
         acc[j] = a;
         if constexpr (MODE == COL_DIV) ws[j].x = q2;
       }
-      __syncthreads();   // buf is refilled by the next batch
+      block_sync<NT>();   // buf is refilled by the next batch
     }
 
     if constexpr (MODE == COL_DIV) {
@@ -780,7 +789,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
         }
       }
     }
-    __syncthreads();
+    block_sync<NT>();
     if constexpr (MODE == COL_STEP || MODE == COL_PROJECT || MODE == COL_ADDW) {
       // Hermitian average; with half-spectrum storage only mx = 0 pairs are stored
       if (kx == 0) {
@@ -790,7 +799,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
           acc[ky] = h;
           acc[NK - ky] = conjg(h);
         }
-        __syncthreads();
+        block_sync<NT>();
       }
       if constexpr (MODE == COL_ADDW) {
         for (int j = tid; j < NK; j += NT) acc[j] = acc[j] + ws[j];
@@ -798,7 +807,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
           s0[2] = A.vmean[0];
           s0[3] = A.vmean[1];
         }
-        __syncthreads();
+        block_sync<NT>();
       }
       for (int j = tid; j < NK; j += NT) A.what[(size_t)kx * NK + j] = acc[j];
     }
@@ -809,7 +818,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
       s0[3] = A.vmean[1];
     }
     cp_async_wait_all();   // tables
-    __syncthreads();
+    block_sync<NT>();
   }
 
   // ---- inverse column transforms of the fields the next row pass reads ----
@@ -843,7 +852,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
       const int b = e / N, y = e % N;
       A.G[((size_t)(f0 + b) * H + kx) * N + y] = buf[b * LP + padi<PS>(y)];
     }
-    __syncthreads();
+    block_sync<NT>();
   }
 }
 

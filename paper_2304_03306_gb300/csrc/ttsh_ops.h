@@ -77,6 +77,23 @@ struct SizeOps {
   void (*pack_args)(const DomainDev&, void* dst);    // host copy of a domain's argument block
 };
 
+// Persistent batched stepper of one precision (ttsh_persist_*.cu): one launch advances a
+// batch of domains with n <= max_n (each with its size's default tile shape) by nsteps.
+struct PersistOps {
+  // doms: device table of ndom packed domains (domain_bytes each); items: device list of
+  // ips work items (item_bytes each); ctl: 2 + 2 ndom zeroed 64-bit counters
+  cudaError_t (*launch)(const void* doms, const void* items, int ips, long long nsteps,
+                        unsigned long long* ctl, int grid, cudaStream_t s);
+  cudaError_t (*prepare)(int* grid);   // kernel attributes; resident blocks on this device
+  void (*pack)(const DomainDev& d, int nrow, int ncol, void* dst);
+  int (*row_blocks)(int n);            // row-pass blocks per step of size n (0: not held)
+  int domain_bytes, item_bytes;
+  int max_n;
+  int threads;                         // block size
+};
+bool persist_f32(PersistOps* o);
+bool persist_f64(PersistOps* o);
+
 // Per translation unit registries; return false if the TU does not hold size n.
 bool ops_f32_small(int n, SizeOps* o);
 bool ops_f32_large(int n, SizeOps* o);

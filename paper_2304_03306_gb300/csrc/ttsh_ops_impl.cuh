@@ -6,41 +6,9 @@
 #include <atomic>
 #include <cstring>
 
-#include "ttsh_kernels.cuh"
-#include "ttsh_ops.h"
+#include "ttsh_args.cuh"
 
 namespace ttsh {
-
-template <typename T>
-static Args<T> make_args(const DomainDev& d) {
-  Args<T> a;
-  a.what = static_cast<cplx<T>*>(d.what);
-  a.vmean = static_cast<T*>(d.vmean);
-  a.K = static_cast<T*>(d.K);
-  a.G = static_cast<cplx<T>*>(d.G);
-  a.Rr = static_cast<cplx<T>*>(d.Rr);
-  a.tw = static_cast<const cplx<T>*>(d.tw);
-  a.real = d.real;
-  a.part = d.part;
-  a.rec = d.rec;
-  a.recctl = static_cast<RecCtl*>(d.recctl);
-  a.err = d.err;
-  a.aux = d.out ? d.out + 5 : nullptr;
-  a.tma = 0;
-  const double dk = 2.0 * 3.14159265358979323846264338327950288 / ((double)d.n * d.dx);
-  a.a = (T)d.a;
-  a.b = (T)d.b;
-  a.lam = (T)d.lam;
-  a.gv = (T)d.gv;
-  a.gw = (T)d.gw;
-  a.dt = (T)d.dt;
-  a.dk = (T)dk;
-  a.mean_decay = (T)exp((d.a - 1.0) * d.dt);
-  a.dx = d.dx;
-  a.cx = d.cx;
-  a.cy = d.cy;
-  return a;
-}
 
 template <typename K>
 static cudaError_t set_smem(K kernel, int bytes, std::atomic<int>& done) {
@@ -192,7 +160,7 @@ static void pack_args(const DomainDev& d, void* dst) {
 template <typename T, int N, int R, int PE, int CL = 1>
 static void add_row_variant(SizeOps& o) {
   if constexpr (RowGeo<T, N, ROW_STEP, R, PE, CL>::VALID &&
-                (N >= 64 || (R == default_rows<T, N>() && PE == default_row_pe<T, N>() && CL == 1))) {
+                (N >= 64 || (R == default_step_rows<T, N>() && PE == default_row_pe<T, N>() && CL == 1))) {
     for (int i = 0; i < o.n_row_variants; ++i)
       if (o.row_step[i].rows == R && o.row_step[i].pe == cmin(PE, N / 2) && o.row_step[i].cl == CL)
         return;   // same shape
@@ -207,7 +175,7 @@ static void add_row_variant(SizeOps& o) {
 
 template <typename T, int N, int PE>
 static void add_col_variant(SizeOps& o) {
-  if constexpr (ColGeo<T, N, COL_STEP, PE>::VALID && (N >= 64 || PE == default_col_pe<T, N>())) {
+  if constexpr (ColGeo<T, N, COL_STEP, PE>::VALID && (N >= 64 || PE == default_step_col_pe<T, N>())) {
     for (int i = 0; i < o.n_col_variants; ++i)
       if (o.col_step[i].pe == cmin(PE, N)) return;
     StepVariant v{&launch_col_mode<T, N, COL_STEP, PE>, nullptr, nullptr, 1, cmin(PE, N), 1};
@@ -230,8 +198,8 @@ static SizeOps make_ops() {
   o.n_col_variants = 0;
   o.args_bytes = (int)sizeof(Args<T>);
   o.pack_args = &pack_args<T>;
-  add_row_variant<T, N, default_rows<T, N>(), default_row_pe<T, N>(), default_row_cluster<T, N>()>(o);
-  add_col_variant<T, N, default_col_pe<T, N>()>(o);
+  add_row_variant<T, N, default_step_rows<T, N>(), default_row_pe<T, N>(), default_row_cluster<T, N>()>(o);
+  add_col_variant<T, N, default_step_col_pe<T, N>()>(o);
   if constexpr (sizeof(T) == 4) {
     add_row_variant<T, N, 4, 16>(o);
     add_row_variant<T, N, 2, 16>(o);

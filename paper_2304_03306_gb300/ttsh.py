@@ -88,6 +88,8 @@ def load_library(path: str = LIB_PATH):
         "ttsh_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
         "ttsh_batch_synchronize": (ctypes.c_int, [_P]),
         "ttsh_batch_groups": (ctypes.c_int32, [_P]),
+        "ttsh_batch_set_persistent": (ctypes.c_int, [_P, ctypes.c_int32]),
+        "ttsh_batch_persistent": (ctypes.c_int32, [_P]),
         "ttsh_batch_destroy": (None, [_P]),
         "ttsh_restrict": (ctypes.c_int, [_P, _P]),
         "ttsh_psd_begin": (ctypes.c_int, [_P, _D, ctypes.c_int32]),
@@ -330,6 +332,15 @@ class Batch:
     @property
     def groups(self) -> int:
         return ttsh_batch_groups(self.b)
+
+    @property
+    def persistent(self) -> bool:
+        return int(load_library().ttsh_batch_persistent(self.b)) == 1
+
+    def set_persistent(self, on: bool):
+        """One launch per step() call for every domain (True, the default where allowed) or
+        one launch per pass per group of equal domains (False)."""
+        _check(load_library().ttsh_batch_set_persistent(self.b, 1 if on else 0))
 
     def close(self):
         if self.b:

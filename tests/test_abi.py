@@ -108,7 +108,7 @@ def test_every_entry_point_rejects_null_handles(lib):
     for every number), returns TTSH_E_INVALID (or -1 / 0 for the counting getters, nothing
     for the destroy functions) before touching the GPU."""
     from paper_2304_03306_gb300 import ttsh
-    special = {"ttsh_batch_groups": -1, "ttsh_fno_num_params": -1, "ttsh_step_count": -1,
+    special = {"ttsh_batch_groups": -1, "ttsh_batch_persistent": -1, "ttsh_fno_num_params": -1, "ttsh_step_count": -1,
                "ttsh_workspace_bytes": 0}
     skip = {"ttsh_default_params", "ttsh_last_error"}
     for name in declared_functions():

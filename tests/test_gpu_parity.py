@@ -634,6 +634,56 @@ def test_batch_equals_individual_domains_bit_for_bit(T):
     b.close()
 
 
+@pytest.mark.parametrize("prec", [32, 64])
+def test_persistent_batch_equals_individual_domains_bit_for_bit(T, prec):
+    """One persistent launch per call advances domains of every size it holds (16^2 to 512^2,
+    circles and dumbbells, several per size) with the single-domain results bit for bit; a
+    second call starts from where the first stopped; the grouped launches give the same bits."""
+    specs = [(512, 0.04, "c", 5.4), (16, 1.0, "c", 5.0), (256, 0.08, "d", 3.0), (128, 0.16, "c", 5.3),
+             (32, 0.5, "c", 5.2), (64, 0.25, "c", 5.2), (256, 0.08, "c", 5.6), (128, 0.16, "d", 2.8),
+             (64, 0.25, "d", 2.9)]
+    batched, alone = [], []
+    for i, (n, dx, shape, R) in enumerate(specs):
+        mask = ti.circle_mask(n, dx, R) if shape == "c" else ti.dumbbell_mask(n, dx, R, 1.4 * R)
+        vx, vy = ti.noise_velocity(mask, 60 + i, 0.3)
+        batched.append(_domain_copy(T, mask, n, dx, prec, vx, vy))
+        alone.append(_domain_copy(T, mask, n, dx, prec, vx, vy))
+    b = T.Batch(batched)
+    assert b.persistent
+    total = 0
+    for nsteps, persistent in ((70, True), (3, True), (40, False), (1, True)):
+        b.set_persistent(persistent)
+        b.step(nsteps)
+        b.synchronize()
+        total += nsteps
+        for d in alone:
+            d.step(nsteps)
+        for d1, d2 in zip(batched, alone):
+            assert d1.steps == d2.steps == total
+            w1, v1 = d1.spectral_state()
+            w2, v2 = d2.spectral_state()
+            assert np.array_equal(w1, w2) and np.array_equal(v1, v2), (d1.n, nsteps, persistent)
+    for d in batched:
+        d.synchronize()          # no bounded wait ran out
+    b.close()
+
+
+def test_persistent_batch_needs_one_precision_and_default_tiles(T):
+    m = ti.circle_mask(64, 0.25, 5.0)
+    mixed = [T.Domain(m, 64, 0.25, precision=32), T.Domain(m, 64, 0.25, precision=64)]
+    b = T.Batch(mixed)
+    assert not b.persistent
+    with pytest.raises(T.TTSHError) as e:
+        b.set_persistent(True)
+    assert e.value.status == T.TTSH_E_UNSUPPORTED
+    b.close()
+    big = [T.Domain(np.zeros((1024, 1024), np.uint8), 1024, 0.04, precision=32),
+           T.Domain(m, 64, 0.25, precision=32)]
+    b = T.Batch(big)
+    assert not b.persistent
+    b.close()
+
+
 def test_batch_sweep_workload_matches_oracle_on_samples(T):
     doms = ti.sweep_domains()
     assert len(doms) == 48
@@ -645,6 +695,7 @@ def test_batch_sweep_workload_matches_oracle_on_samples(T):
         o.set_velocity(vx, vy)
         objs.append(o)
     b = T.Batch(objs)
+    assert b.persistent              # the whole sweep in one launch per call
     b.step(10)
     b.synchronize()
     for idx in (0, 13, 22, 40):      # a 128^2, 256^2 and 512^2 circle and a dumbbell
