@@ -11,8 +11,10 @@
 // backward pass) run on the 5th-generation tensor cores (tcgen05.mma BF16 -> FP32 in tensor
 // memory, fused bias / residual / GELU epilogue).  The transforms restricted to the kept
 // modes are exact DFT matrices (2m x n per row and per column, cheaper than a full FFT when
-// m << n) applied by dedicated FP32 kernels, and the per-mode complex mixing reads BF16
-// weights with FP32 sums.
+// m << n).  The row transforms (onto the kept kx and back, and their adjoints in the backward
+// pass) run on the tensor cores as well (BF16 operands, FP32 accumulation); the column
+// transforms along y with the per-mode complex mixing run in dedicated FP32 kernels that read
+// BF16 weights.
 // Gradients use fixed-order partial sums, so repeated calls give identical bits.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -282,6 +284,216 @@ __global__ void __launch_bounds__(128) pointwise_tc_kernel(PwArgs a) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+}
+
+// ---------------------------------------------------------------------------------------
+// Restricted row transforms on the tensor cores.  With q = (sample, y) a grid row and the 32
+// channels c, the four row contractions of a spectral layer are
+//   contract over x:  out[q][j][c] = sum_x M[j][x] act[q][x][c]   (row DFT onto the kept kx,
+//                     and the adjoint of the inverse row transform)
+//   expand to x:      out[q][x][c] = sum_j M[x][j] in[q][j][c]    (inverse row transform onto
+//                     the grid, and the adjoint of the row DFT)
+// with j over the 2m <= 32 kept (Re, Im) kx entries.  Both are tcgen05.mma kind::f16 with
+// BF16 operands staged in shared memory in the canonical K-major layout without swizzle
+// (8-row x 16-byte core matrices; K-adjacent core matrices 128 B apart, 8-row groups
+// K * 16 B apart) and a 128 x 32 FP32 accumulator per MMA group in tensor memory.
+//   contract: M = 128 rows (4 grid rows x 32 channels), N = 32 (j, padded), K = n (x);
+//             the activation tile is transposed into the K-major layout while it is staged.
+//   expand:   M = 128 x values of one x tile, N = 32 channels, K = 32 (j, padded); the CTA
+//             keeps its x tile of M and walks over grid rows two at a time (two accumulators).
+// Completion is an mbarrier signalled by tcgen05.commit with a bounded wait (time-out: error
+// word, tensor memory released, CTA returns).
+// ---------------------------------------------------------------------------------------
+struct XcArgs {
+  const __nv_bfloat16* M;     // contract: [32][n] (rows j >= J zero); expand: [n][32] (columns j >= J zero)
+  const __nv_bfloat16* act;   // contract: [Q][n][32] BF16
+  const float* in;            // expand:   [Q][J][32] FP32 (rounded to BF16 when staged)
+  float* out;                 // contract: [Q][J][32]; expand: [Q][n][32]
+  int n, J;
+  long long Q;
+  int* err;
+};
+
+__device__ __forceinline__ void tc_alloc(uint32_t* dst, int cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(cols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(uint32_t tmem, int cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols) : "memory");
+}
+__device__ __forceinline__ void tc_mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t id, int accumulate) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+               ::"r"(tmem), "l"(ad), "l"(bd), "r"(id), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 32 accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+               "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                 "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                 "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                 "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+constexpr int kXcMaxN = 512;
+inline int xcontract_smem(int n) { return 128 * n * 2 + 32 * n * 2 + 128; }
+
+__global__ void __launch_bounds__(128) xcontract_tc_kernel(XcArgs a) {
+  extern __shared__ __align__(16) uint8_t xc_dyn[];
+  uint8_t* sa = xc_dyn + ((128u - (smem_u32(xc_dyn) & 127u)) & 127u);   // 128 x n activation tile
+  uint8_t* sb = sa + 128 * a.n * 2;                                      // 32 x n matrix
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = a.n, nk = n >> 3, SBO = n * 16;
+  for (int c = tid; c < 32 * nk; c += 128) {
+    const int r = c / nk, kc = c % nk;
+    *reinterpret_cast<uint4*>(sb + (r >> 3) * SBO + kc * 128 + (r & 7) * 16) =
+        *reinterpret_cast<const uint4*>(a.M + (long long)r * n + kc * 8);
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+  if (warp == 0) tc_alloc(&tmem_base, 32);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const long long ntiles = (a.Q + 3) / 4;
+  uint32_t phase = 0;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long q0 = t * 4;
+    // activation tile, transposed: row m = 32 qi + c, column k = x <- act[q0 + qi][x][c]
+    // (16-byte loads of 8 channels, eight 2-byte stores into one core-matrix column)
+    // (eight loads in flight per thread before their stores; 16 n units of 8 channels)
+    for (int u0 = tid; u0 < 4 * n * 4; u0 += 8 * 128) {
+      uint4 v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int u = u0 + i * 128, x = (u >> 2) % n, qi = (u >> 2) / n;
+        v[i] = make_uint4(0, 0, 0, 0);
+        if (u < 16 * n && q0 + qi < a.Q)
+          v[i] = *reinterpret_cast<const uint4*>(a.act + ((q0 + qi) * n + x) * CW + (u & 3) * 8);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int u = u0 + i * 128, c8 = u & 3, x = (u >> 2) % n, qi = (u >> 2) / n;
+        if (u >= 16 * n) break;   // past the tile (n not a multiple of 64)
+        const __nv_bfloat16* e = reinterpret_cast<const __nv_bfloat16*>(&v[i]);
+        uint8_t* dst = sa + (qi * 4 + c8) * SBO + (x >> 3) * 128 + (x & 7) * 2;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) *reinterpret_cast<__nv_bfloat16*>(dst + k * 16) = e[k];
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor core
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      constexpr uint32_t id = umma_idesc_bf16(kTcRows, CW);
+      for (int ks = 0; ks < n / 16; ++ks)
+        tc_mma_bf16(tmem, umma_desc(smem_u32(sa) + ks * 256, 128, SBO), umma_desc(smem_u32(sb) + ks * 256, 128, SBO),
+                    id, ks);
+      tc_commit(&mbar);
+    }
+    const bool done = ttsh::mbar_wait_bounded(smem_u32(&mbar), phase, ttsh::kWaitLimitNs);
+    if (__syncthreads_or(!done)) {
+      if (tid == 0) atomicExch(a.err, 1);
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint32_t r[CW];
+    tc_ld32(tmem + ((uint32_t)(warp * 32) << 16), r);
+    const long long q = q0 + warp;   // this warp's accumulator rows: grid row q0 + warp, channel = lane
+    if (q < a.Q)
+      for (int j = 0; j < a.J; ++j) a.out[(q * a.J + j) * CW + lane] = __uint_as_float(r[j]);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, 32);
+}
+
+__global__ void __launch_bounds__(128) xexpand_tc_kernel(XcArgs a) {
+  __shared__ __align__(1024) uint8_t sa[128 * 32 * 2];       // 128 x 32 matrix tile
+  __shared__ __align__(1024) uint8_t sbt[2 * 32 * 32 * 2];   // two 32 (c) x 32 (j) operands
+  __shared__ float stile[4 * 32 * 33];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = a.n, x0 = blockIdx.x * 128;
+  for (int c = tid; c < 128 * 4; c += 128) {
+    const int r = c >> 2, kc = c & 3;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (x0 + r < n) v = *reinterpret_cast<const uint4*>(a.M + (long long)(x0 + r) * 32 + kc * 8);
+    *reinterpret_cast<uint4*>(sa + core_off(r, kc)) = v;
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+  if (warp == 0) tc_alloc(&tmem_base, 64);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const long long npairs = (a.Q + 1) / 2;
+  uint32_t phase = 0;
+  for (long long pr = blockIdx.y; pr < npairs; pr += gridDim.y) {
+    const long long q0 = pr * 2;
+    // operands: row c, column k = j <- in[q0 + qi][j][c] (zero for j >= J or past the end)
+    for (int u = tid; u < 2 * 32 * 32; u += 128) {
+      const int c = u & 31, j = (u >> 5) & 31, qi = u >> 10;
+      float v = 0.f;
+      if (j < a.J && q0 + qi < a.Q) v = a.in[((q0 + qi) * a.J + j) * CW + c];
+      *reinterpret_cast<__nv_bfloat16*>(sbt + qi * 2048 + core_off(c, j >> 3) + (j & 7) * 2) = __float2bfloat16_rn(v);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+      constexpr uint32_t id = umma_idesc_bf16(kTcRows, CW);
+      for (int qi = 0; qi < 2; ++qi)
+        for (int ks = 0; ks < 2; ++ks)
+          tc_mma_bf16(tmem + qi * 32, umma_desc(smem_u32(sa) + ks * 256, 128, 512),
+                      umma_desc(smem_u32(sbt) + qi * 2048 + ks * 256, 128, 512), id, ks);
+      tc_commit(&mbar);
+    }
+    const bool done = ttsh::mbar_wait_bounded(smem_u32(&mbar), phase, ttsh::kWaitLimitNs);
+    if (__syncthreads_or(!done)) {
+      if (tid == 0) atomicExch(a.err, 1);
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: this warp's 32 x rows of each grid row, through a padded 32 x 33 tile so that
+    // the stores are 128-byte rows of consecutive channels
+    float* tile = stile + warp * 32 * 33;
+    const int xw = x0 + warp * 32;
+    const int nrows = n - xw >= 32 ? 32 : (n - xw > 0 ? n - xw : 0);
+    for (int qi = 0; qi < 2; ++qi) {
+      uint32_t r[CW];
+      tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + qi * 32, r);
+      const long long q = q0 + qi;
+      if (q >= a.Q) continue;
+#pragma unroll
+      for (int c = 0; c < CW; ++c) tile[lane * 33 + c] = __uint_as_float(r[c]);
+      __syncwarp();
+      for (int i = 0; i < nrows; ++i) a.out[(q * n + xw + i) * CW + lane] = tile[i * 33 + lane];
+      __syncwarp();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) tc_dealloc(tmem, 64);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -731,6 +943,10 @@ struct ttsh_fno {
   int wchunk, nwblk;
   float in_scale[4] = {1, 1, 1, 1}, out_scale = 1;
   bool fused_columns = false;   // row_dft / column kernels fit in shared memory
+  // BF16 matrices of the row contractions on the tensor cores (tc_rows: n % 16 == 0,
+  // n <= 512, 2m <= 32): Fx [32][n], Bx [n][32], Fx^T [n][32], Bx^T [32][n], zero-padded
+  __nv_bfloat16 *FxB = nullptr, *BxB = nullptr, *FxTB = nullptr, *BxTB = nullptr;
+  bool tc_rows = false;
   long long adam_t = 0;
   std::vector<void*> allocs;
 };
@@ -757,6 +973,26 @@ ttsh_status fno_cuda(cudaError_t e, const char* what) {
 unsigned tc_grid(long long P) {
   const long long tiles = (P + kTcRows - 1) / kTcRows;
   return (unsigned)(tiles < 152 * 4 ? tiles : 152 * 4);
+}
+
+// out[q][j][c] = sum_x M[j][x] act[q][x][c] on the tensor cores (Q grid rows)
+cudaError_t run_xcontract(ttsh_fno* f, const __nv_bfloat16* M, const __nv_bfloat16* act, long long Q, float* out) {
+  XcArgs a{M, act, nullptr, out, f->n, 2 * f->m, Q, f->tc_err};
+  const long long tiles = (Q + 3) / 4;
+  const unsigned grid = (unsigned)(tiles < 152 * 2 ? tiles : 152 * 2);
+  xcontract_tc_kernel<<<grid, 128, xcontract_smem(f->n), f->stream>>>(a);
+  return cudaGetLastError();
+}
+
+// out[q][x][c] = sum_j M[x][j] in[q][j][c] on the tensor cores
+cudaError_t run_xexpand(ttsh_fno* f, const __nv_bfloat16* M, const float* in, long long Q, float* out) {
+  XcArgs a{M, nullptr, in, out, f->n, 2 * f->m, Q, f->tc_err};
+  const int xt = (f->n + 127) / 128;
+  const long long pairs = (Q + 1) / 2;
+  const long long per = (152LL * 6) / xt;
+  dim3 grid((unsigned)xt, (unsigned)(pairs < per ? pairs : per));
+  xexpand_tc_kernel<<<grid, 128, 0, f->stream>>>(a);
+  return cudaGetLastError();
 }
 
 // Report (once) a tensor-core completion wait that ran out; called at synchronising entries.
@@ -815,7 +1051,9 @@ ttsh_status forward_impl(ttsh_fno* f, const float* x, int B, float* out, const f
   for (int l = 0; l < L; ++l) {
     const float* hl = f->h[l];
     // row DFT: Hx[q] (2m x C) = Fx (2m x n) . h[q] (n x C), q = (b, y)
-    if (f->fused_columns) {
+    if (f->tc_rows) {
+      FNO_CUDA(run_xcontract(f, f->FxB, f->hb[l], (long long)B * n, f->Hx), "row DFT (tensor cores)");
+    } else if (f->fused_columns) {
       row_dft_kernel<<<(unsigned)(B * n), 256, row_dft_smem(n, m), s>>>(hl, f->Fx, n, m, f->Hx);
       FNO_CUDA(cudaGetLastError(), "row DFT");
     } else {
@@ -845,7 +1083,9 @@ ttsh_status forward_impl(ttsh_fno* f, const float* x, int B, float* out, const f
       FNO_CUDA(sgemm(false, false, n, (int)mC, 2 * m, B, 1.f, f->Gpi, 2 * m, 0, f->Yr, mC, sH, 1.f, f->Z + mC, 2 * mC, sX, s), "inv col");
     }
     // inverse row: s[q] (n x C) = Bx (n x 2m) . Z[q] (2m x C)
-    if (f->fused_columns) {
+    if (f->tc_rows) {
+      FNO_CUDA(run_xexpand(f, f->BxB, f->Z, (long long)B * n, f->s), "inverse row (tensor cores)");
+    } else if (f->fused_columns) {
       row_idft_kernel<<<(unsigned)(B * n), 256, row_idft_smem(n, m), s>>>(f->Z, f->Bx, n, m, f->s);
       FNO_CUDA(cudaGetLastError(), "inv row");
     } else {
@@ -910,8 +1150,12 @@ ttsh_status backward_impl(ttsh_fno* f, const float* x, int B, const float* out) 
     FNO_CUDA(cudaGetLastError(), "gelu backward");
     if ((st = wgrad(f, f->h[l], C, f->dz, C, P, f->grad + f->off_W[l], f->grad + f->off_b[l])) != TTSH_OK) return st;
     // spectral adjoint: dZ[q] = Bx^T dz[q]
-    FNO_CUDA(sgemm(true, false, 2 * m, C, n, B * n, 1.f, f->Bx, 2 * m, 0, f->dz, C, (long long)n * C, 0.f, f->Z, C,
-                   2LL * m * C, s), "inv row adjoint");
+    if (f->tc_rows) {
+      FNO_CUDA(run_xcontract(f, f->BxTB, f->dzb, (long long)B * n, f->Z), "inv row adjoint (tensor cores)");
+    } else {
+      FNO_CUDA(sgemm(true, false, 2 * m, C, n, B * n, 1.f, f->Bx, 2 * m, 0, f->dz, C, (long long)n * C, 0.f, f->Z, C,
+                     2LL * m * C, s), "inv row adjoint");
+    }
     // dY = G'^H dZ
     FNO_CUDA(sgemm(true, false, 2 * m, (int)mC, n, B, 1.f, f->Gpr, 2 * m, 0, f->Z, 2 * mC, sX, 0.f, f->Yr, mC, sH, s), "inv col adjoint");
     FNO_CUDA(sgemm(true, false, 2 * m, (int)mC, n, B, 1.f, f->Gpi, 2 * m, 0, f->Z + mC, 2 * mC, sX, 1.f, f->Yr, mC, sH, s), "inv col adjoint");
@@ -930,8 +1174,12 @@ ttsh_status backward_impl(ttsh_fno* f, const float* x, int B, const float* out) 
     FNO_CUDA(sgemm(true, false, n, (int)mC, 2 * m, B, 1.f, f->Gr, n, 0, dHi, mC, sH, 0.f, f->Hx + mC, 2 * mC, sX, s), "col adjoint");
     FNO_CUDA(sgemm(true, false, n, (int)mC, 2 * m, B, -1.f, f->Gi, n, 0, dHr, mC, sH, 1.f, f->Hx + mC, 2 * mC, sX, s), "col adjoint");
     // dh_spec[q] = Fx^T dHx[q]
-    FNO_CUDA(sgemm(true, false, n, C, 2 * m, B * n, 1.f, f->Fx, n, 0, f->Hx, C, 2LL * m * C, 0.f, f->dspec, C,
-                   (long long)n * C, s), "row adjoint");
+    if (f->tc_rows) {
+      FNO_CUDA(run_xexpand(f, f->FxTB, f->Hx, (long long)B * n, f->dspec), "row adjoint (tensor cores)");
+    } else {
+      FNO_CUDA(sgemm(true, false, n, C, 2 * m, B * n, 1.f, f->Fx, n, 0, f->Hx, C, 2LL * m * C, 0.f, f->dspec, C,
+                     (long long)n * C, s), "row adjoint");
+    }
     // dh_l = dz W^T + dh_spec on the tensor cores
     PwArgs a;
     a.A = f->dzb;
@@ -1017,6 +1265,10 @@ ttsh_status ttsh_fno_create(const ttsh_fno_config* cfg, uint64_t seed, void* str
   A(&f->Gpr, 2LL * m * n * 4);
   A(&f->Gpi, 2LL * m * n * 4);
   A(&f->Bx, 2LL * m * n * 4);
+  A(&f->FxB, 32LL * n * 2);
+  A(&f->BxB, 32LL * n * 2);
+  A(&f->FxTB, 32LL * n * 2);
+  A(&f->BxTB, 32LL * n * 2);
   f->h.assign(L + 1, nullptr);
   f->z.assign(L, nullptr);
   f->hb.assign(L, nullptr);
@@ -1085,7 +1337,27 @@ ttsh_status ttsh_fno_create(const ttsh_fno_config* cfg, uint64_t seed, void* str
     float* dst[6] = {f->Fx, f->Gr, f->Gi, f->Gpr, f->Gpi, f->Bx};
     for (int i = 0; i < 6 && e == cudaSuccess; ++i)
       e = cudaMemcpy(dst[i], src[i]->data(), src[i]->size() * 4, cudaMemcpyHostToDevice);
+    // BF16 operands of the tensor-core row contractions, padded to 32 kept entries
+    std::vector<__nv_bfloat16> fxb(32 * n), bxb(32 * n), fxtb(32 * n), bxtb(32 * n);
+    for (int j = 0; j < 32; ++j)
+      for (int x = 0; x < n; ++x) {
+        const float fv = j < 2 * m ? Fx[j * n + x] : 0.f;
+        const float bv = j < 2 * m ? Bx[x * 2 * m + j] : 0.f;
+        fxb[j * n + x] = __float2bfloat16_rn(fv);    // [j][x]
+        fxtb[x * 32 + j] = __float2bfloat16_rn(fv);  // [x][j]
+        bxb[x * 32 + j] = __float2bfloat16_rn(bv);   // [x][j]
+        bxtb[j * n + x] = __float2bfloat16_rn(bv);   // [j][x]
+      }
+    const std::vector<__nv_bfloat16>* bsrc[4] = {&fxb, &bxb, &fxtb, &bxtb};
+    __nv_bfloat16* bdst[4] = {f->FxB, f->BxB, f->FxTB, f->BxTB};
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i)
+      e = cudaMemcpy(bdst[i], bsrc[i]->data(), bsrc[i]->size() * 2, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cleanup(fno_cuda(e, "DFT matrices"));
+    if (n % 16 == 0 && n <= kXcMaxN && 2 * m <= 32) {
+      e = cudaFuncSetAttribute(xcontract_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, xcontract_smem(n));
+      if (e != cudaSuccess) return cleanup(fno_cuda(e, "row contraction attribute"));
+      f->tc_rows = true;
+    }
   }
   // seeded initialisation: pointwise weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)), biases 0,
   // spectral weights U(0, 1/(C*C)) (real and imaginary parts)
