@@ -139,7 +139,8 @@ def csrc_hash():
 def plan_variant(kernel, plan):
     if kernel == "row_pass":
         cl = plan.get("row_cluster", 1)
-        return [plan["rows_per_block"], plan["row_points_per_thread"]] + ([cl] if cl > 1 else [])
+        return [plan["rows_per_block"], plan["row_points_per_thread"]] + ([cl] if cl > 1 else []) + \
+            (["compact"] if plan.get("row_compact", 0) else [])
     return [plan["col_points_per_thread"]]
 
 

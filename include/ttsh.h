@@ -208,12 +208,14 @@ ttsh_status ttsh_time_kernels(ttsh_domain* d, int32_t iters, double* ms);
  * (points per thread); entry 0 is the default.  Variants compute the same step with a
  * different factorisation of the transforms, so results agree to rounding, not bit for bit.
  * ttsh_autotune times every variant (as ttsh_time_kernels does, `iters` launches each, state
- * restored) and selects the fastest row and column variant.  plan (9 int32, may be NULL):
+ * restored) and selects the fastest row and column variant.  plan (10 int32, may be NULL):
  * {row variant, column variant, rows per block, row points per thread, column points per
  * thread, number of row variants, number of column variants, launch mode, row blocks per
- * cluster}.  On grids of 2048^2 and more, float row variants with two blocks per cluster
- * stage the column-major inter-pass tiles for both blocks' rows at once and swap halves
- * through distributed shared memory.  ttsh_set_plan
+ * cluster, compact row pass}.  On grids of 2048^2 and more, float row variants with two
+ * blocks per cluster stage the column-major inter-pass tiles for both blocks' rows at once
+ * and swap halves through distributed shared memory.  On 1024^2 to 4096^2 grids, compact
+ * float row variants transform in place (no separate forward buffers), so that two blocks
+ * fit per SM and one block's staging and stores overlap the other's transforms.  ttsh_set_plan
  * selects variants by index (TTSH_E_INVALID if out of range).  ttsh_autotune times each row
  * variant with its G tile staged both ways (see ttsh_set_launch_mode), keeps the fastest
  * (variant, staging) pair, and then times whole steps (graphs of up to 64 steps, state

@@ -1321,6 +1321,7 @@ ttsh_status ttsh_get_plan(ttsh_domain* d, int32_t* plan) {
     plan[6] = d->ops.n_col_variants;
     plan[7] = d->dev.pdl | (d->dev.use_tma << 1);
     plan[8] = d->ops.row_step[d->rv].cl;
+    plan[9] = d->ops.row_step[d->rv].cmp;
   }
   return TTSH_OK;
 }

@@ -134,8 +134,12 @@ __host__ __device__ constexpr int row_stride(int LP, int R, int words) {
 // Row-pass geometry and shared-memory plan.  CL > 1: the step kernel runs as clusters of CL
 // blocks over CL * R consecutive rows; each block stages one CL-th of the stored columns for
 // all the cluster's rows (global segments of CL * R values instead of R), and the blocks
-// read from each other's shares through distributed shared memory.
-template <typename T, int N, int KIND, int R, int PEV, int CL = 1>
+// read from each other's shares through distributed shared memory.  CMP = 1 (compact): the
+// forward transforms work in place (no separate buffers) and the mask rows are read from
+// global memory where the real-space terms need them (not staged), so that two or more
+// blocks fit per SM on large grids and one block's staging and stores overlap another's
+// transforms.
+template <typename T, int N, int KIND, int R, int PEV, int CL = 1, int CMP = 0>
 struct RowGeo {
   static constexpr int L = N / 2, M = N / 4, H = M + 1;
   static constexpr int PE = cmin(PEV, L);
@@ -161,7 +165,7 @@ struct RowGeo {
   static constexpr int GIN_BYTES = NPL * GPS;
   static constexpr int KS_BYTES = KIND == ROW_STEP ? align16(R * N * (int)sizeof(T)) : 0;
   static constexpr int RED_BYTES = KIND == ROW_INV_DIAG ? kDiagQ * 1024 * 8 : 0;
-  static constexpr bool STAGE_K = KS_BYTES > 0 && TW_BYTES + BUF_BYTES + KS_BYTES + RED_BYTES <= kSmemLimit;
+  static constexpr bool STAGE_K = KS_BYTES > 0 && CMP == 0 && TW_BYTES + BUF_BYTES + KS_BYTES + RED_BYTES <= kSmemLimit;
   static constexpr bool STAGE_G = GIN_BYTES > 0 &&
       TW_BYTES + BUF_BYTES + GIN_BYTES + (STAGE_K ? KS_BYTES : 0) + RED_BYTES <= kSmemLimit;
   // step kernel: the forward transforms get buffers of their own when they fit, so that the
@@ -169,7 +173,7 @@ struct RowGeo {
   // buffers, no in-place pass)
   // (float only: in double the duplicated c1 arithmetic costs more DP-pipe time than the
   // saved pass)
-  static constexpr bool SEPARATE = KIND == ROW_STEP && sizeof(T) == 4 && STAGE_K &&
+  static constexpr bool SEPARATE = KIND == ROW_STEP && sizeof(T) == 4 && STAGE_K && CMP == 0 &&
       TW_BYTES + 2 * BUF_BYTES + (STAGE_G ? GIN_BYTES : 0) + KS_BYTES <= kSmemLimit;
   static constexpr int OFF_BUF = TW_BYTES;
   static constexpr int OFF_GIN = align128(OFF_BUF + BUF_BYTES);
@@ -375,10 +379,10 @@ __device__ __forceinline__ void dsmem_st(unsigned a, cplx<double> v) {
 // overwritten); results in place.
 // tmapG: G as a 2D tensor [3 (N/4+1)][2N scalars] with a box of R rows x (N/4+1), a grid-
 // constant kernel parameter (used when A.tma is set; may be null otherwise).
-template <typename T, int N, int KIND, int R, int PEV, int CL = 1>
+template <typename T, int N, int KIND, int R, int PEV, int CL = 1, int CMP = 0>
 __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned char* smem_raw,
                                          const CUtensorMap* tmapG) {
-  using Geo = RowGeo<T, N, KIND, R, PEV, CL>;
+  using Geo = RowGeo<T, N, KIND, R, PEV, CL, CMP>;
   static_assert(Geo::VALID, "row pass tile does not fit");
   constexpr int L = Geo::L, M = Geo::M, H = Geo::H;
   constexpr int NT = Geo::NT, PE = Geo::PE, PS = Geo::PS, LP = Geo::LPR;
@@ -868,11 +872,11 @@ __device__ __forceinline__ unsigned char* smem_base128(unsigned char* raw) {
 
 // The tensor map is a separate grid-constant parameter so that its address can be handed to
 // the TMA while the argument block stays an ordinary by-value parameter.
-template <typename T, int N, int KIND, int R, int PEV, int CL = 1>
-__global__ void __launch_bounds__(RowGeo<T, N, KIND, R, PEV, CL>::NT)
+template <typename T, int N, int KIND, int R, int PEV, int CL = 1, int CMP = 0>
+__global__ void __launch_bounds__(RowGeo<T, N, KIND, R, PEV, CL, CMP>::NT)
 row_kernel(Args<T> A, const __grid_constant__ CUtensorMap tmapG) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  row_body<T, N, KIND, R, PEV, CL>(A, blockIdx.x, smem_base128(smem_raw), &tmapG);
+  row_body<T, N, KIND, R, PEV, CL, CMP>(A, blockIdx.x, smem_base128(smem_raw), &tmapG);
 }
 
 template <typename T, int N, int MODE, int PEV>

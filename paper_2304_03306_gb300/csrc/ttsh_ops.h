@@ -58,12 +58,13 @@ struct StepVariant {
   PrepareFn prepare;   // sets the batched kernel's attributes (call before graph capture)
   int rows;
   int pe;
-  int cl;   // blocks per cluster (row pass)
+  int cl;    // blocks per cluster (row pass)
+  int cmp;   // 1: compact row pass (in-place forward transforms)
 };
 
 constexpr int kMaxBatchN = 1024;
 
-constexpr int kMaxVariants = 8;
+constexpr int kMaxVariants = 12;
 
 struct SizeOps {
   RowFn row;

@@ -52,11 +52,12 @@ static cudaError_t launch_k(void (*kernel)(P...), int grid, int block, int smem,
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <typename T, int N, int KIND, int R = default_rows<T, N>(), int PE = default_row_pe<T, N>(), int CL = 1>
+template <typename T, int N, int KIND, int R = default_rows<T, N>(), int PE = default_row_pe<T, N>(), int CL = 1,
+          int CMP = 0>
 static cudaError_t launch_row_kind(const DomainDev& d, cudaStream_t s) {
-  using Geo = RowGeo<T, N, KIND, R, PE, CL>;
+  using Geo = RowGeo<T, N, KIND, R, PE, CL, CMP>;
   static std::atomic<int> done{0};
-  cudaError_t e = set_smem(row_kernel<T, N, KIND, R, PE, CL>, Geo::SMEM, done);
+  cudaError_t e = set_smem(row_kernel<T, N, KIND, R, PE, CL, CMP>, Geo::SMEM, done);
   if (e != cudaSuccess) return e;
   Args<T> a = make_args<T>(d);
   CUtensorMap tm;
@@ -68,8 +69,8 @@ static cudaError_t launch_row_kind(const DomainDev& d, cudaStream_t s) {
       a.tma = 1;
     }
   }
-  return launch_k(row_kernel<T, N, KIND, R, PE, CL>, N / R, Geo::NT, Geo::SMEM, s, KIND == ROW_STEP && d.pdl, CL, a,
-                  tm);
+  return launch_k(row_kernel<T, N, KIND, R, PE, CL, CMP>, N / R, Geo::NT, Geo::SMEM, s, KIND == ROW_STEP && d.pdl, CL,
+                  a, tm);
 }
 
 template <typename T, int N, int MODE, int PE = default_col_pe<T, N>()>
@@ -157,15 +158,19 @@ static void pack_args(const DomainDev& d, void* dst) {
   memcpy(dst, &a, sizeof(a));
 }
 
-template <typename T, int N, int R, int PE, int CL = 1>
+template <typename T, int N, int R, int PE, int CL = 1, int CMP = 0>
 static void add_row_variant(SizeOps& o) {
-  if constexpr (RowGeo<T, N, ROW_STEP, R, PE, CL>::VALID &&
-                (N >= 64 || (R == default_step_rows<T, N>() && PE == default_row_pe<T, N>() && CL == 1))) {
+  if constexpr (RowGeo<T, N, ROW_STEP, R, PE, CL, CMP>::VALID &&
+                (N >= 64 || (R == default_step_rows<T, N>() && PE == default_row_pe<T, N>() && CL == 1 && CMP == 0))) {
+    // a compact variant whose plan equals the plain one's (nothing to leave out) is the same shape
+    constexpr int cmp =
+        RowGeo<T, N, ROW_STEP, R, PE, CL, CMP>::SMEM != RowGeo<T, N, ROW_STEP, R, PE, CL, 0>::SMEM ? CMP : 0;
     for (int i = 0; i < o.n_row_variants; ++i)
-      if (o.row_step[i].rows == R && o.row_step[i].pe == cmin(PE, N / 2) && o.row_step[i].cl == CL)
+      if (o.row_step[i].rows == R && o.row_step[i].pe == cmin(PE, N / 2) && o.row_step[i].cl == CL &&
+          o.row_step[i].cmp == cmp)
         return;   // same shape
-    StepVariant v{&launch_row_kind<T, N, ROW_STEP, R, PE, CL>, nullptr, nullptr, R, cmin(PE, N / 2), CL};
-    if constexpr (N <= kMaxBatchN && CL == 1) {
+    StepVariant v{&launch_row_kind<T, N, ROW_STEP, R, PE, CL, CMP>, nullptr, nullptr, R, cmin(PE, N / 2), CL, cmp};
+    if constexpr (N <= kMaxBatchN && CL == 1 && CMP == 0) {
       v.batched = &launch_row_batched<T, N, R, PE>;
       v.prepare = &prepare_row_batched<T, N, R, PE>;
     }
@@ -178,7 +183,7 @@ static void add_col_variant(SizeOps& o) {
   if constexpr (ColGeo<T, N, COL_STEP, PE>::VALID && (N >= 64 || PE == default_step_col_pe<T, N>())) {
     for (int i = 0; i < o.n_col_variants; ++i)
       if (o.col_step[i].pe == cmin(PE, N)) return;
-    StepVariant v{&launch_col_mode<T, N, COL_STEP, PE>, nullptr, nullptr, 1, cmin(PE, N), 1};
+    StepVariant v{&launch_col_mode<T, N, COL_STEP, PE>, nullptr, nullptr, 1, cmin(PE, N), 1, 0};
     if constexpr (N <= kMaxBatchN) {
       v.batched = &launch_col_batched<T, N, PE>;
       v.prepare = &prepare_col_batched<T, N, PE>;
@@ -209,6 +214,12 @@ static SizeOps make_ops() {
       // clusters of two blocks: global segments of 2R values (large grids, where R is small)
       add_row_variant<T, N, 1, 16, 2>(o);
       add_row_variant<T, N, 2, 16, 2>(o);
+    }
+    if constexpr (N >= 1024 && N <= 4096) {
+      // compact: in-place forward transforms, mask rows not staged: two or more blocks per SM
+      add_row_variant<T, N, 2, 16, 1, 1>(o);
+      add_row_variant<T, N, 1, 16, 2, 1>(o);
+      add_row_variant<T, N, 1, 16, 1, 1>(o);
     }
     add_col_variant<T, N, 8>(o);
     add_col_variant<T, N, 16>(o);

@@ -265,7 +265,7 @@ def ttsh_time_kernels(h, iters: int):
 
 _PLAN_KEYS = ("row_variant", "col_variant", "rows_per_block", "row_points_per_thread",
               "col_points_per_thread", "n_row_variants", "n_col_variants", "launch_mode",
-              "row_cluster")
+              "row_cluster", "row_compact")
 
 
 def _plan_dict(buf):
