@@ -10,8 +10,11 @@
 // (PE/R butterflies of radix R), all threads synchronise, each applies the inter-stage
 // twiddles, an R-point DFT in registers (radix-2 decimation in frequency, output in
 // bit-reversed register order) and writes the results to their Stockham positions.  Shared
-// memory is padded by one slot every PE elements so that the stride-PE writes of the first
-// stage hit distinct banks.
+// memory is padded by one slot every 128 bytes (16 float or 8 double complex values),
+// whatever PE is: the stages' 8- and 16-byte accesses are served 128 bytes per wavefront,
+// and with this interval the contiguous runs a thread writes in the first stage, and the
+// strided reads of the later stages, fall on distinct banks (one slot every PE elements did
+// the same only for PE = 16 in float and PE = 8 in double).
 //
 // Twiddles W_N^m = exp(-2 pi i m / N) come from shared memory (the whole table when it fits
 // in 16 KB, else two tables of ~sqrt(N) entries whose product gives W_N^m; per-stage tables
@@ -59,6 +62,8 @@ __host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
 // Padded shared-memory index: one spare slot every 2^PS elements.
+template <typename T>
+__host__ __device__ constexpr int pad_shift() { return ilog2(128 / (int)sizeof(cplx<T>)); }
 template <int PS>
 __device__ __forceinline__ int padi(int i) { return i + (i >> PS); }
 template <int L, int PS>
@@ -325,7 +330,7 @@ __device__ __forceinline__ void stockham_all(cplx<T>* buf, int j, bool active,
 template <typename T, int L, int PE, int DIR, int NT, int TWN, int STRIDE = 0, typename LD = NoLoad>
 __device__ __forceinline__ void fft_batch(cplx<T>* sm, int B, const TwTab<T, TWN>& tw, const cplx<T>* stab,
                                           const LD& ld = LD{}) {
-  constexpr int PS = ilog2(PE);
+  constexpr int PS = pad_shift<T>();
   constexpr int LP = STRIDE > 0 ? STRIDE : padded_len<L, PS>();
   constexpr int TT = L / PE;
   static_assert(NT % TT == 0, "block size must be a multiple of the threads per transform");

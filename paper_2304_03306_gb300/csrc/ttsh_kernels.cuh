@@ -116,9 +116,15 @@ __host__ __device__ constexpr int default_col_pe() { return sizeof(T) == 4 ? (N 
 // defaults above, except the float 512^2 step, which starts with two rows per block and 16
 // points per thread in both passes: the shape whose blocks are small enough (96 threads,
 // < 45 KB of shared memory) for the persistent batched stepper to keep several resident per
-// SM; the autotuner may pick the faster single-domain shape.
+// SM; the autotuner may pick the faster single-domain shape.  (At 256^2 and 128^2 two rows
+// and 8 points per thread are faster for one domain alone - 3.3 against 4.2 us, 2.6 against
+// 3.7 us per row pass - but slower in a batch, where twice the blocks pay their fixed costs
+// twice: 53.0 against 49.9 us per step of the 48-domain sweep; so they stay autotuner
+// choices.)
 template <typename T, int N>
 __host__ __device__ constexpr int default_step_rows() { return sizeof(T) == 4 && N == 512 ? 2 : default_rows<T, N>(); }
+template <typename T, int N>
+__host__ __device__ constexpr int default_step_row_pe() { return default_row_pe<T, N>(); }
 template <typename T, int N>
 __host__ __device__ constexpr int default_step_col_pe() { return sizeof(T) == 4 && N == 512 ? 16 : default_col_pe<T, N>(); }
 // blocks per cluster of the default step row pass (8192^2 float: one row per block, pairs)
@@ -143,7 +149,7 @@ template <typename T, int N, int KIND, int R, int PEV, int CL = 1, int CMP = 0>
 struct RowGeo {
   static constexpr int L = N / 2, M = N / 4, H = M + 1;
   static constexpr int PE = cmin(PEV, L);
-  static constexpr int PS = ilog2(PE);
+  static constexpr int PS = pad_shift<T>();
   static constexpr int LP = padded_len<L, PS>();
   static constexpr int TT = L / PE;
   static constexpr int FI = row_inv_fields<KIND>();
@@ -202,7 +208,7 @@ template <typename T, int N, int MODE, int PEV>
 struct ColGeo {
   static constexpr int M = N / 4, H = M + 1, NK = 2 * M + 1;
   static constexpr int PE = cmin(PEV, N);
-  static constexpr int PS = ilog2(PE);
+  static constexpr int PS = pad_shift<T>();
   static constexpr int LP = padded_len<N, PS>();
   static constexpr int TT = N / PE;
   static constexpr int NF = MODE == COL_STEP ? 3 : (MODE == COL_PROJECT || MODE == COL_DIV) ? 2

@@ -161,7 +161,7 @@ static void pack_args(const DomainDev& d, void* dst) {
 template <typename T, int N, int R, int PE, int CL = 1, int CMP = 0>
 static void add_row_variant(SizeOps& o) {
   if constexpr (RowGeo<T, N, ROW_STEP, R, PE, CL, CMP>::VALID &&
-                (N >= 64 || (R == default_step_rows<T, N>() && PE == default_row_pe<T, N>() && CL == 1 && CMP == 0))) {
+                (N >= 64 || (R == default_step_rows<T, N>() && PE == default_step_row_pe<T, N>() && CL == 1 && CMP == 0))) {
     // a compact variant whose plan equals the plain one's (nothing to leave out) is the same shape
     constexpr int cmp =
         RowGeo<T, N, ROW_STEP, R, PE, CL, CMP>::SMEM != RowGeo<T, N, ROW_STEP, R, PE, CL, 0>::SMEM ? CMP : 0;
@@ -203,7 +203,7 @@ static SizeOps make_ops() {
   o.n_col_variants = 0;
   o.args_bytes = (int)sizeof(Args<T>);
   o.pack_args = &pack_args<T>;
-  add_row_variant<T, N, default_step_rows<T, N>(), default_row_pe<T, N>(), default_row_cluster<T, N>()>(o);
+  add_row_variant<T, N, default_step_rows<T, N>(), default_step_row_pe<T, N>(), default_row_cluster<T, N>()>(o);
   add_col_variant<T, N, default_step_col_pe<T, N>()>(o);
   if constexpr (sizeof(T) == 4) {
     add_row_variant<T, N, 4, 16>(o);

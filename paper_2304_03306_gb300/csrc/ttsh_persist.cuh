@@ -91,7 +91,7 @@ constexpr int kPersistMaxN = 512;
 template <typename T, int N>
 struct PersistShape {
   static constexpr int R = default_step_rows<T, N>();
-  static constexpr int RPE = default_row_pe<T, N>();
+  static constexpr int RPE = default_step_row_pe<T, N>();
   static constexpr int CPE = default_step_col_pe<T, N>();
   using RG = RowGeo<T, N, ROW_STEP, R, RPE>;
   using CG = ColGeo<T, N, COL_STEP, CPE>;
