@@ -268,15 +268,28 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
   constexpr int TT = L / PE;
   constexpr int NB = PE / R;
   constexpr bool FUSED = Ns == 1 && !std::is_same<LD, NoLoad>::value;
+  // Padded index of i + d: when adding d cannot carry out of the low PS bits of i (d a
+  // multiple of the padding interval, or every index below one interval), padi(i + d) =
+  // padi(i) + d + (d >> PS), so one padded base and compile-time offsets serve all of a
+  // thread's accesses in the stage.
+  constexpr int SL = L / R;   // stride of a butterfly's inputs
+  constexpr bool LD_OFF = SL % (1 << PS) == 0 || L <= (1 << PS);
+  constexpr bool ST_OFF = Ns % (1 << PS) == 0 || Ns * R <= (1 << PS);
   cplx<T> v[NB][R];
   if (active) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int q = j + b * TT;
+      if constexpr (FUSED) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        if constexpr (FUSED) v[b][r] = ld(bi, q + r * (L / R));
-        else v[b][r] = buf[padi<PS>(q + r * (L / R))];
+        for (int r = 0; r < R; ++r) v[b][r] = ld(bi, q + r * SL);
+      } else if constexpr (LD_OFF) {
+        const cplx<T>* p0 = buf + padi<PS>(q);
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b][r] = p0[r * SL + ((r * SL) >> PS)];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b][r] = buf[padi<PS>(q + r * SL)];
       }
     }
   }
@@ -303,8 +316,14 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
       }
       dft_reg<T, R, DIR>(v[b]);
       const int base = (q - k) * R + k;
+      if constexpr (ST_OFF) {
+        cplx<T>* p0 = buf + padi<PS>(base);
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[padi<PS>(base + r * Ns)] = v[b][bitrev<R>(r)];
+        for (int r = 0; r < R; ++r) p0[r * Ns + ((r * Ns) >> PS)] = v[b][bitrev<R>(r)];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[padi<PS>(base + r * Ns)] = v[b][bitrev<R>(r)];
+      }
     }
   }
   stage_sync<TT, NT>();
