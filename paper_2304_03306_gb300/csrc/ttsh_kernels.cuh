@@ -414,7 +414,6 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
     const char* src = reinterpret_cast<const char*>(A.K + (size_t)y0 * N);
     for (int i = tid; i < NCH; i += NT) cp_async16(reinterpret_cast<char*>(ks) + 16 * i, src + 16 * i);
   }
-  griddep_launch();
   griddep_wait();
   if constexpr (Geo::STAGE_G) {
     bool via_tma = false;
@@ -595,6 +594,10 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
   // ---- forward row transforms (R2C), keep mx <= N/4 ----
   if constexpr (FF > 0) {
     if constexpr (!Geo::SEPARATE) fft_batch<T, L, PE, -1, NT, N, LP>(fw, FF * R, tw, stab);
+    // programmatic dependent launch: the next pass may be launched now that this block only
+    // has its stores left (triggering earlier lets the next pass's waiting blocks take shared
+    // memory from this pass's blocks that have not started yet)
+    griddep_launch();
     // clusters: every block is past its inverse loads, so the shares can take the results
     if constexpr (CL > 1) cluster_sync();
     for (int e = tid; e < FF * R * H; e += NT) {
@@ -655,7 +658,6 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
   const TwTab<T, N> tw = TwTab<T, N>::fill(reinterpret_cast<cplx<T>*>(smem_raw), A.tw, tid, NT);
   cplx<T>* stab = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_STAB);
   StageTab<T, N, PE>::template fill<N>(stab, A.tw, tid, NT);
-  griddep_launch();
   griddep_wait();   // everything below reads what the previous kernel wrote
   auto ky_of = [](int j) { return j <= M ? j : j - NK; };
   // async copy of nb contiguous columns of Rr (fields f0..f0+nb-1) into the padded buffers
@@ -858,6 +860,7 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
       return v;
     };
     fft_batch<T, N, PE, +1, NT, N, 0>(buf, nb, tw, stab, load);
+    if (f0 + nb >= NI) griddep_launch();   // only the last stores are left (see the row pass)
     for (int e = tid; e < nb * N; e += NT) {
       const int b = e / N, y = e % N;
       A.G[((size_t)(f0 + b) * H + kx) * N + y] = buf[b * LP + padi<PS>(y)];

@@ -18,6 +18,29 @@ static cudaError_t set_smem(K kernel, int bytes, std::atomic<int>& done) {
   return e;
 }
 
+// Shared memory a programmatic dependent launch of at most one block per SM reserves per
+// block: more than half an SM's, so that blocks admitted early (while the previous pass
+// still runs) cannot pile up two per SM and leave other SMs idle when they start.
+constexpr int kSpreadSmem = 116 * 1024;
+
+static int sm_count() {
+  static std::atomic<int> sms{0};
+  int v = sms.load(std::memory_order_acquire);
+  if (v == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      v = 1 << 30;
+    sms.store(v, std::memory_order_release);
+  }
+  return v;
+}
+
+// Dynamic shared memory of a step-pass launch: the pass's own, or kSpreadSmem for a
+// programmatic dependent launch of at most one block per SM.
+static int launch_smem(int smem, int grid, bool pdl) {
+  return pdl && grid <= sm_count() && smem < kSpreadSmem ? kSpreadSmem : smem;
+}
+
 // Launch, optionally as a programmatic dependent launch (the kernel may start while the
 // previous kernel in the stream is still running; it waits (griddepcontrol.wait) before it
 // touches anything that kernel writes) and optionally in clusters of `cl` blocks along x.
@@ -57,7 +80,7 @@ template <typename T, int N, int KIND, int R = default_rows<T, N>(), int PE = de
 static cudaError_t launch_row_kind(const DomainDev& d, cudaStream_t s) {
   using Geo = RowGeo<T, N, KIND, R, PE, CL, CMP>;
   static std::atomic<int> done{0};
-  cudaError_t e = set_smem(row_kernel<T, N, KIND, R, PE, CL, CMP>, Geo::SMEM, done);
+  cudaError_t e = set_smem(row_kernel<T, N, KIND, R, PE, CL, CMP>, cmax(Geo::SMEM, kSpreadSmem), done);
   if (e != cudaSuccess) return e;
   Args<T> a = make_args<T>(d);
   CUtensorMap tm;
@@ -69,20 +92,22 @@ static cudaError_t launch_row_kind(const DomainDev& d, cudaStream_t s) {
       a.tma = 1;
     }
   }
-  return launch_k(row_kernel<T, N, KIND, R, PE, CL, CMP>, N / R, Geo::NT, Geo::SMEM, s, KIND == ROW_STEP && d.pdl, CL,
-                  a, tm);
+  const bool pdl = KIND == ROW_STEP && d.pdl;
+  return launch_k(row_kernel<T, N, KIND, R, PE, CL, CMP>, N / R, Geo::NT, launch_smem(Geo::SMEM, N / R, pdl), s, pdl,
+                  CL, a, tm);
 }
 
 template <typename T, int N, int MODE, int PE = default_col_pe<T, N>()>
 static cudaError_t launch_col_mode(const DomainDev& d, cudaStream_t s) {
   using Geo = ColGeo<T, N, MODE, PE>;
   static std::atomic<int> done{0};
-  cudaError_t e = set_smem(col_kernel<T, N, MODE, PE>, Geo::SMEM, done);
+  cudaError_t e = set_smem(col_kernel<T, N, MODE, PE>, cmax(Geo::SMEM, kSpreadSmem), done);
   if (e != cudaSuccess) return e;
   // a recorded step adds one block that finishes the time-series sample
   const int extra = (MODE == COL_STEP && d.rec != nullptr) ? 1 : 0;
-  return launch_k(col_kernel<T, N, MODE, PE>, Geo::H + extra, Geo::NT, Geo::SMEM, s, MODE == COL_STEP && d.pdl, 1,
-                  make_args<T>(d));
+  const bool pdl = MODE == COL_STEP && d.pdl;
+  return launch_k(col_kernel<T, N, MODE, PE>, Geo::H + extra, Geo::NT, launch_smem(Geo::SMEM, Geo::H + extra, pdl), s,
+                  pdl, 1, make_args<T>(d));
 }
 
 template <typename T, int N>
