@@ -191,3 +191,32 @@ def evaluate(net, radius, coarse_steps=2000, sample_every=50, transient=3000, am
     for d in (fine, cp, cf):
         d.close()
     return res
+
+
+def main(argv=None):
+    """Run the corrector network's forward pass on random inputs and report its time:
+    python -m paper_2304_03306_gb300.corrector --passes K [--batch B] (configured network:
+    256^2, width 32, 16 modes, 4 layers).  Useful for timing and profiling the network alone."""
+    import argparse
+
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--passes", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=1)
+    a = ap.parse_args(argv)
+    net = ttsh.FNO(n=COARSE["n"], width=32, modes=16, layers=4, max_batch=max(1, a.batch), seed=0)
+    x = torch.randn((a.batch, COARSE["n"], COARSE["n"], 4), device="cuda")
+    y = torch.zeros((a.batch, COARSE["n"], COARSE["n"]), device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    net.forward(x.data_ptr(), y.data_ptr(), a.batch)
+    e0.record()
+    for _ in range(a.passes):
+        net.forward(x.data_ptr(), y.data_ptr(), a.batch)
+    e1.record()
+    torch.cuda.synchronize()
+    print(f"forward, batch {a.batch}: {e0.elapsed_time(e1) / max(1, a.passes):.4f} ms per pass")
+    net.close()
+
+
+if __name__ == "__main__":
+    main()
