@@ -323,6 +323,17 @@ int32_t ttsh_batch_groups(const ttsh_batch* b);   /* number of launch groups, -1
  * ttsh_batch_persistent returns 1, 0, or -1 for NULL. */
 ttsh_status ttsh_batch_set_persistent(ttsh_batch* b, int32_t on);
 int32_t ttsh_batch_persistent(const ttsh_batch* b);
+
+/* Test hook of the persistent stepper's failure path (no counterpart in the paper): launches,
+ * on the batch's stream, the persistent kernel with one block and a one-item work list - the
+ * first column item of the first domain's first step, whose row items are not in the list - with
+ * the dependency wait limited to `seconds` (0 < seconds <= 1, else TTSH_E_INVALID;
+ * TTSH_E_UNSUPPORTED for a batch that cannot step persistently).  The wait runs out, sets the
+ * first domain's status word and the launch's abort flag, and the block returns without
+ * running the item, so the first domain's next ttsh_synchronize returns TTSH_E_TIMEOUT once;
+ * no state is changed and the context and the batch stay usable.  (Production waits are
+ * limited to 2 s.) */
+ttsh_status ttsh_batch_test_stalled_wait(ttsh_batch* b, double seconds);
 void ttsh_batch_destroy(ttsh_batch* b);           /* NULL is a no-op; domains are untouched */
 
 /* Temporal power spectral density of the vorticity, Eq. (PSD) of Sec. III.B:

@@ -721,6 +721,7 @@ struct ttsh_batch {
   ttsh::PersistOps pops{};
   void* pdoms = nullptr;               // device domain table
   void* pitems = nullptr;              // device work-item list of one step
+  void* ptest = nullptr;               // one-item list of ttsh_batch_test_stalled_wait
   unsigned long long* pctl = nullptr;  // device control block: 2 + 2 ndom counters
   int pips = 0, pgrid = 0;
 };
@@ -1474,7 +1475,8 @@ ttsh_status ttsh_batch_step(ttsh_batch* b, int64_t nsteps) {
     if (nsteps > 0) {
       const size_t ctl_bytes = (2 + 2 * b->all.size()) * sizeof(unsigned long long);
       TTSH_CUDA(cudaMemsetAsync(b->pctl, 0, ctl_bytes, b->stream), "persistent batch reset");
-      TTSH_CUDA(b->pops.launch(b->pdoms, b->pitems, b->pips, (long long)nsteps, b->pctl, b->pgrid, b->stream),
+      TTSH_CUDA(b->pops.launch(b->pdoms, b->pitems, b->pips, (long long)nsteps, b->pctl, b->pgrid, ttsh::kWaitLimitNs,
+                               b->stream),
                 "persistent batch launch");
     }
     for (ttsh_domain* d : b->all) d->steps += nsteps;
@@ -1525,6 +1527,29 @@ ttsh_status ttsh_batch_set_persistent(ttsh_batch* b, int32_t on) {
 
 int32_t ttsh_batch_persistent(const ttsh_batch* b) { return b ? (b->persistent ? 1 : 0) : -1; }
 
+ttsh_status ttsh_batch_test_stalled_wait(ttsh_batch* b, double seconds) {
+  if (!b) return fail(TTSH_E_INVALID, "batch is NULL");
+  if (!(seconds > 0.0) || seconds > 1.0) return fail(TTSH_E_INVALID, "seconds must be in (0, 1]");
+  if (!b->can_persist) return fail(TTSH_E_UNSUPPORTED, "the batch does not allow persistent stepping");
+  // one block, one work item: the first column item of the first domain's first step, whose
+  // row items are not in the list, so its dependency wait cannot complete
+  if (!b->ptest) {
+    const int item[4] = {0, 1, 0, 0};
+    TTSH_CUDA(cudaMalloc(&b->ptest, sizeof(item)), "test item");
+    TTSH_CUDA(cudaMemcpy(b->ptest, item, sizeof(item), cudaMemcpyHostToDevice), "test item");
+  }
+  for (ttsh_domain* d : b->all) {
+    if (d->stream == b->stream) continue;
+    TTSH_CUDA(cudaEventRecord(b->order, d->stream), "order event");
+    TTSH_CUDA(cudaStreamWaitEvent(b->stream, b->order, 0), "order wait");
+  }
+  const size_t ctl_bytes = (2 + 2 * b->all.size()) * sizeof(unsigned long long);
+  TTSH_CUDA(cudaMemsetAsync(b->pctl, 0, ctl_bytes, b->stream), "persistent batch reset");
+  TTSH_CUDA(b->pops.launch(b->pdoms, b->ptest, 1, 1, b->pctl, 1, (unsigned long long)(seconds * 1e9), b->stream),
+            "stalled persistent launch");
+  return TTSH_OK;
+}
+
 void ttsh_batch_destroy(ttsh_batch* b) {
   if (!b) return;
   if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -1535,6 +1560,7 @@ void ttsh_batch_destroy(ttsh_batch* b) {
     if (g.join) cudaEventDestroy(g.join);
   }
   if (b->pdoms) cudaFree(b->pdoms);
+  if (b->ptest) cudaFree(b->ptest);
   if (b->pitems) cudaFree(b->pitems);
   if (b->pctl) cudaFree(b->pctl);
   if (b->fork) cudaEventDestroy(b->fork);

@@ -84,7 +84,7 @@ struct PersistOps {
   // doms: device table of ndom packed domains (domain_bytes each); items: device list of
   // ips work items (item_bytes each); ctl: 2 + 2 ndom zeroed 64-bit counters
   cudaError_t (*launch)(const void* doms, const void* items, int ips, long long nsteps,
-                        unsigned long long* ctl, int grid, cudaStream_t s);
+                        unsigned long long* ctl, int grid, unsigned long long limit_ns, cudaStream_t s);
   cudaError_t (*prepare)(int* grid);   // kernel attributes; resident blocks on this device
   void (*pack)(const DomainDev& d, int nrow, int ncol, void* dst);
   int (*row_blocks)(int n);            // row-pass blocks per step of size n (0: not held)

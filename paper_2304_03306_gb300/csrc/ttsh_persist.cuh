@@ -21,9 +21,9 @@
 // requirement (acquire loads), and after the item one thread adds 1 to its own counter
 // (release).  Items are taken in increasing order and every dependency points to a smaller
 // index, so the waited-for items were taken by blocks that are running: no deadlock without
-// co-residency guarantees.  Every wait is bounded in time (2 s); one that runs out sets the
-// domain's status word (TTSH_E_TIMEOUT at its next synchronising call) and an abort flag
-// that makes every block stop taking items.
+// co-residency guarantees.  Every wait is bounded in time (limit_ns: 2 s in production); one
+// that runs out sets the domain's status word (TTSH_E_TIMEOUT at its next synchronising call)
+// and an abort flag that makes every block stop taking items.
 //
 // The item bodies are the single-domain row and column pass bodies with each size's
 // default tile shape, so every domain's results are bit-identical to ttsh_step.  The block
@@ -160,7 +160,7 @@ __device__ __forceinline__ void item_need(const PDomain<T>* doms, const PItem& i
 template <typename T>
 __global__ void __launch_bounds__(PersistLimits<T>::NT + 32, sizeof(T) == 4 ? 5 : 2)
 persistent_step_kernel(const PDomain<T>* __restrict__ doms, const PItem* __restrict__ items, int ips,
-                       long long nsteps, unsigned long long* __restrict__ ctl) {
+                       long long nsteps, unsigned long long* __restrict__ ctl, unsigned long long limit_ns) {
   constexpr int NB = PersistLimits<T>::NT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* smem = smem_base128(smem_raw);
@@ -177,7 +177,7 @@ persistent_step_kernel(const PDomain<T>* __restrict__ doms, const PItem* __restr
     unsigned long long* ctr;
     unsigned long long need;
     item_need(doms, it, g / ips, ctl, &ctr, &need);
-    if (wait_count(ctr, need, abort_flag, kWaitLimitNs)) return true;
+    if (wait_count(ctr, need, abort_flag, limit_ns)) return true;
     atomicExch(doms[it.dom].A.err, 1);
     atomicExch(abort_flag, 1ull);
     return false;

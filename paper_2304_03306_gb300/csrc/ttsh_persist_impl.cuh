@@ -61,10 +61,10 @@ static cudaError_t persist_prepare(int* grid) {
 
 template <typename T>
 static cudaError_t persist_launch(const void* doms, const void* items, int ips, long long nsteps,
-                                  unsigned long long* ctl, int grid, cudaStream_t s) {
+                                  unsigned long long* ctl, int grid, unsigned long long limit_ns, cudaStream_t s) {
   constexpr int smem = PersistLimits<T>::SMEM + 128;
   persistent_step_kernel<T><<<grid, PersistLimits<T>::NT + 32, smem, s>>>(
-      static_cast<const PDomain<T>*>(doms), static_cast<const PItem*>(items), ips, nsteps, ctl);
+      static_cast<const PDomain<T>*>(doms), static_cast<const PItem*>(items), ips, nsteps, ctl, limit_ns);
   return cudaGetLastError();
 }
 

@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH):
         "ttsh_batch_groups": (ctypes.c_int32, [_P]),
         "ttsh_batch_set_persistent": (ctypes.c_int, [_P, ctypes.c_int32]),
         "ttsh_batch_persistent": (ctypes.c_int32, [_P]),
+        "ttsh_batch_test_stalled_wait": (ctypes.c_int, [_P, ctypes.c_double]),
         "ttsh_batch_destroy": (None, [_P]),
         "ttsh_restrict": (ctypes.c_int, [_P, _P]),
         "ttsh_psd_begin": (ctypes.c_int, [_P, _D, ctypes.c_int32]),
@@ -336,6 +337,10 @@ class Batch:
     @property
     def persistent(self) -> bool:
         return int(load_library().ttsh_batch_persistent(self.b)) == 1
+
+    def test_stalled_wait(self, seconds: float):
+        """Failure-path test hook of the persistent stepper (see ttsh.h)."""
+        _check(load_library().ttsh_batch_test_stalled_wait(self.b, float(seconds)))
 
     def set_persistent(self, on: bool):
         """One launch per step() call for every domain (True, the default where allowed) or

@@ -668,6 +668,39 @@ def test_persistent_batch_equals_individual_domains_bit_for_bit(T, prec):
     b.close()
 
 
+def test_persistent_stepper_wait_timeout_is_reported_and_the_batch_stays_usable(T):
+    """A dependency wait of the persistent stepper that cannot complete (one block, a column
+    item whose row items are not in its work list) runs out after its limit; the first domain
+    reports TTSH_E_TIMEOUT once, nothing was stepped, and the batch then steps on with the
+    single-domain results."""
+    specs = [(128, 0.16, 5.3), (64, 0.25, 5.2)]
+    batched, alone = [], []
+    for i, (n, dx, R) in enumerate(specs):
+        mask = ti.circle_mask(n, dx, R)
+        vx, vy = ti.noise_velocity(mask, 70 + i, 0.3)
+        batched.append(_domain_copy(T, mask, n, dx, 32, vx, vy))
+        alone.append(_domain_copy(T, mask, n, dx, 32, vx, vy))
+    b = T.Batch(batched)
+    assert b.persistent
+    w_before, _ = batched[0].spectral_state()
+    b.test_stalled_wait(0.05)
+    with pytest.raises(T.TTSHError) as e:
+        batched[0].synchronize()
+    assert e.value.status == T.TTSH_E_TIMEOUT
+    batched[0].synchronize()                       # reported once
+    batched[1].synchronize()                       # the other domain was not involved
+    w_after, _ = batched[0].spectral_state()
+    assert np.array_equal(w_before, w_after)
+    b.step(20)
+    b.synchronize()
+    for d1, d2 in zip(batched, alone):
+        d2.step(20)
+        w1, v1 = d1.spectral_state()
+        w2, v2 = d2.spectral_state()
+        assert np.array_equal(w1, w2) and np.array_equal(v1, v2)
+    b.close()
+
+
 def test_persistent_batch_needs_one_precision_and_default_tiles(T):
     m = ti.circle_mask(64, 0.25, 5.0)
     mixed = [T.Domain(m, 64, 0.25, precision=32), T.Domain(m, 64, 0.25, precision=64)]
