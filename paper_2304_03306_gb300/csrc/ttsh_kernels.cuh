@@ -247,91 +247,153 @@ struct ColGeo {
 // ---------------------------------------------------------------------------------------
 // Time-series sample taken inside a step's row pass.  The pass already holds omega, v_x and
 // v_y of its R rows in real space (the state the step starts from), so the energy,
-// enstrophy and order-parameter sums cost one extra sweep over shared memory: per-thread
-// and per-warp sums in T (fixed-order shuffles), then the warps in index order in double,
-// to kDiagQ partials per block, written to A.rec.
+// enstrophy and order-parameter sums cost one sweep over shared memory spread over all the
+// block's threads (in the in-place variants, the loop of the real-space terms, which reads
+// every point once anyway): per-thread, per-warp and per-block sums in T (fixed order), one
+// partial per block written to A.rec; the column pass's sample block adds the partials up.
 // Same quantities as ROW_INV_DIAG: sum |v|^2, sum omega^2, sum |e_theta . v| (e_theta = 0 at
 // the centre), sum |v|, number of points with a non-finite value.
 // ---------------------------------------------------------------------------------------
-template <typename T, int N, int R, int NT, typename RL>
-__device__ __forceinline__ void record_partials(const Args<T>& A, int blk, int y0, RL rl) {
-  const T dx = (T)A.dx, cx = (T)A.cx, cy = (T)A.cy;
+template <typename T>
+struct SeriesSums {
   T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
   int bad = 0;
-  for (int e = threadIdx.x; e < R * N; e += NT) {
-    const int r = e / N, x = e % N;
-    const T w = rl(0, r, x), vx = rl(1, r, x), vy = rl(2, r, x);
-    const T px = (T)(x - N / 2) * dx - cx;
-    const T py = (T)(y0 + r - N / 2) * dx - cy;
+  // point (x, y) of the grid with omega = w, v = (vx, vy); (px, py) its position relative
+  // to the centre
+  __device__ __forceinline__ void add(T w, T vx, T vy, T px, T py) {
     const T rr2 = px * px + py * py;
     const T v2 = vx * vx + vy * vy;
     s0 += v2;
     s1 += w * w;
     s2 += rr2 > (T)0 ? fabs(px * vy - py * vx) * rsqrt(rr2) : (T)0;
-    s3 += sqrt(v2);
+    if constexpr (sizeof(T) == 4) s3 += v2 > (T)0 ? v2 * rsqrt(v2) : (T)0;   // |v| within 2 ulp
+    else s3 += sqrt(v2);
     bad += (isfinite(w) && isfinite(vx) && isfinite(vy)) ? 0 : 1;
   }
-  // warp sums in T (the per-thread sums already are; on GB300 a double add costs 16x a
-  // float one), then the warps' sums in double
-  T q[kDiagQ - 1] = {s0, s1, s2, s3};
-  constexpr int NW = (NT + 31) / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wl = cmin(32, NT - warp * 32);   // lanes present in this warp
-  const unsigned mask = wl == 32 ? 0xffffffffu : ((1u << wl) - 1u);
+  // every thread of the NT calls this once: warp sums in T (fixed-order shuffles), then the
+  // warps in index order, also in T (one barrier), to the block's partial blk of A.rec
+  // (kDiagQ values of type T).  No double arithmetic here (on GB300 a double add costs the
+  // SM's FP64 unit 16 cycles per warp): the column pass's sample block adds the block
+  // partials up.
+  template <int NT>
+  __device__ __forceinline__ void store(const Args<T>& A, int blk) const {
+    T q[kDiagQ] = {s0, s1, s2, s3, (T)bad};   // per-thread counts are small: exact in T
+    constexpr int NW = (NT + 31) / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int wl = cmin(32, NT - warp * 32);   // lanes present in this warp
+    const unsigned mask = wl == 32 ? 0xffffffffu : ((1u << wl) - 1u);
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
+    for (int off = 16; off > 0; off >>= 1) {
 #pragma unroll
-    for (int k = 0; k < kDiagQ - 1; ++k) {
-      const T o = __shfl_down_sync(mask, q[k], off);
-      if (lane + off < wl) q[k] += o;
+      for (int k = 0; k < kDiagQ; ++k) {
+        const T o = __shfl_down_sync(mask, q[k], off);
+        if (lane + off < wl) q[k] += o;
+      }
     }
-    const int ob = __shfl_down_sync(mask, bad, off);
-    if (lane + off < wl) bad += ob;
+    __shared__ T wsum[NW][kDiagQ];
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < kDiagQ; ++k) wsum[warp][k] = q[k];
+    }
+    block_sync<NT>();
+    if (threadIdx.x < kDiagQ) {
+      T t = wsum[0][threadIdx.x];
+#pragma unroll
+      for (int w2 = 1; w2 < NW; ++w2) t += wsum[w2][threadIdx.x];
+      reinterpret_cast<T*>(A.rec)[(size_t)blk * kDiagQ + threadIdx.x] = t;
+    }
   }
-  __shared__ double wsum[NW][kDiagQ];
-  if (lane == 0) {
-    for (int k = 0; k < kDiagQ - 1; ++k) wsum[warp][k] = (double)q[k];
-    wsum[warp][kDiagQ - 1] = (double)bad;
+};
+
+// Double-float sums (value = hi + lo, |lo| <= ulp(hi) / 2): Knuth's error-free TwoSum, so
+// adding up float partials this way is as accurate as adding them in double, at the float
+// rate (on GB300 one double add costs the SM's FP64 unit 16 cycles per warp).
+struct DFloat {
+  float hi, lo;   // trivial, so that it can live in shared memory; start from {0, 0}
+  __device__ __forceinline__ static void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
   }
-  block_sync<NT>();
-  if (threadIdx.x < kDiagQ) {
-    double t = 0.0;
-    for (int w2 = 0; w2 < NW; ++w2) t += wsum[w2][threadIdx.x];
-    A.rec[(size_t)blk * kDiagQ + threadIdx.x] = t;
+  __device__ __forceinline__ void add(float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo += e;
   }
+  __device__ __forceinline__ void add(DFloat o) {
+    float s, e;
+    two_sum(hi, o.hi, s, e);
+    e += lo + o.lo;
+    hi = s + e;                 // renormalise (|e| small against s)
+    lo = e - (hi - s);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Append {step, energy, enstrophy, psi, non-finite count} from the five sums.
+__device__ __forceinline__ void record_append(RecCtl* c, const double* t) {
+  const double two_over_pi = 0.63661977236758134307553505349005744813783858296183;
+  const long long i = c->count;
+  if (i < c->capacity) {
+    double* o = c->series + (size_t)i * 5;
+    o[0] = (double)(c->base + i * (long long)c->every);
+    o[1] = t[0] * c->inv2n2;
+    o[2] = t[1] * c->inv2n2;
+    o[3] = (t[2] / t[3] - two_over_pi) / (1.0 - two_over_pi);
+    o[4] = t[4];
+  } else {
+    c->overflow = 1;
+  }
+  c->count = i + 1;
 }
 
 // Finish a recorded step's sample (one extra block of the column pass, which runs beside the
-// column blocks): sum the row blocks' partials in a fixed order (lane-strided, then a shuffle
-// tree in warp 0) and append {step, energy, enstrophy, psi, non-finite count}.
+// column blocks): warp 0 adds the row pass's block partials up in a fixed order (lane l
+// takes partials l, l + 32, ...; then a shuffle tree), as double-float sums for a float
+// domain and in double for a double one, and appends {step, energy, enstrophy, psi,
+// non-finite count}.  The other warps leave at once: on the path to the next step, one
+// warp's short dependent chain costs less than a cross-warp reduction.
 template <typename T>
 __device__ __forceinline__ void record_sample(const Args<T>& A) {
   griddep_launch();
   griddep_wait();   // the row pass's partials
-  if (threadIdx.x >= 32) return;
+  if (threadIdx.x >= 32) return;   // the block has at least 64 threads: warp 0 is whole
   RecCtl* c = A.recctl;
+  const T* part = reinterpret_cast<const T*>(A.rec);
   const int lane = threadIdx.x;
-  double q[kDiagQ] = {0, 0, 0, 0, 0};
-  for (int b = lane; b < c->nblocks; b += 32)
-    for (int k = 0; k < kDiagQ; ++k) q[k] += A.rec[(size_t)b * kDiagQ + k];
+  const int np = c->nblocks;
+  using Acc = typename std::conditional<sizeof(T) == 4, DFloat, double>::type;
+  Acc q[kDiagQ];
+#pragma unroll
+  for (int k = 0; k < kDiagQ; ++k) q[k] = Acc{};   // zero: {0, 0} or 0.0
+  for (int b = lane; b < np; b += 32)
+#pragma unroll
+    for (int k = 0; k < kDiagQ; ++k) {
+      if constexpr (sizeof(T) == 4) q[k].add(part[(size_t)b * kDiagQ + k]);
+      else q[k] += part[(size_t)b * kDiagQ + k];
+    }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-    for (int k = 0; k < kDiagQ; ++k) q[k] += __shfl_down_sync(0xffffffffu, q[k], off);
-  if (lane == 0) {
-    const double two_over_pi = 0.63661977236758134307553505349005744813783858296183;
-    const long long i = c->count;
-    if (i < c->capacity) {
-      double* o = c->series + (size_t)i * 5;
-      o[0] = (double)(c->base + i * (long long)c->every);
-      o[1] = q[0] * c->inv2n2;
-      o[2] = q[1] * c->inv2n2;
-      o[3] = (q[2] / q[3] - two_over_pi) / (1.0 - two_over_pi);
-      o[4] = q[4];
-    } else {
-      c->overflow = 1;
+    for (int k = 0; k < kDiagQ; ++k) {
+      if constexpr (sizeof(T) == 4) {
+        DFloat o;
+        o.hi = __shfl_down_sync(0xffffffffu, q[k].hi, off);
+        o.lo = __shfl_down_sync(0xffffffffu, q[k].lo, off);
+        q[k].add(o);
+      } else {
+        q[k] += __shfl_down_sync(0xffffffffu, q[k], off);
+      }
     }
-    c->count = i + 1;
+  if (lane == 0) {
+    double r[kDiagQ];
+#pragma unroll
+    for (int k = 0; k < kDiagQ; ++k) {
+      if constexpr (sizeof(T) == 4) r[k] = q[k].value();
+      else r[k] = q[k];
+    }
+    record_append(c, r);
   }
 }
 
@@ -385,7 +447,8 @@ __device__ __forceinline__ void dsmem_st(unsigned a, cplx<double> v) {
 // overwritten); results in place.
 // tmapG: G as a 2D tensor [3 (N/4+1)][2N scalars] with a box of R rows x (N/4+1), a grid-
 // constant kernel parameter (used when A.tma is set; may be null otherwise).
-template <typename T, int N, int KIND, int R, int PEV, int CL = 1, int CMP = 0>
+// REC = false leaves out the time-series sums (for callers whose Args never carry them).
+template <typename T, int N, int KIND, int R, int PEV, int CL = 1, int CMP = 0, bool REC = true>
 __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned char* smem_raw,
                                          const CUtensorMap* tmapG) {
   using Geo = RowGeo<T, N, KIND, R, PEV, CL, CMP>;
@@ -505,7 +568,6 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
   cplx<T>* fw = sm;   // buffers of the forward transforms
   if constexpr (KIND == ROW_INV_DIAG) fw = sm + R * LP;   // v_x, v_y (fields 1 and 2)
   if constexpr (KIND == ROW_STEP && Geo::SEPARATE) {
-    if (A.rec != nullptr) record_partials<T, N, R, NT>(A, blk, y0, rl);
     fw = reinterpret_cast<cplx<T>*>(smem_raw + Geo::OFF_FWD);
     // F0..F2 at complex slot k of row r (real points 2k in .x, 2k + 1 in .y), computed from
     // omega, v_x, v_y and K as the forward transforms' input; same arithmetic as the
@@ -525,24 +587,47 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
       };
       return mk<T>(F(wz.x, vxz.x, vyz.x, k0), F(wz.y, vxz.y, vyz.y, k1));
     };
+    if (REC && A.rec != nullptr) {
+      // a recorded step: one sweep over the real-space fields, spread over every thread of
+      // the block, adds each point to the time-series sums (the fields stay in place: the
+      // forward transforms write a separate buffer)
+      SeriesSums<T> ss;
+      const T dx = (T)A.dx, cx = (T)A.cx, cy = (T)A.cy;
+#pragma unroll 4
+      for (int e = tid; e < R * N; e += NT) {
+        const int r = e / N, x = e % N;
+        ss.add(rl(0, r, x), rl(1, r, x), rl(2, r, x), (T)(x - N / 2) * dx - cx, (T)(y0 + r - N / 2) * dx - cy);
+      }
+      ss.template store<NT>(A, blk);
+    }
     fft_batch<T, L, PE, -1, NT, N, LP>(fw, FF * R, tw, stab, rhs);
   } else if constexpr (KIND == ROW_STEP) {
-    if (A.rec != nullptr) record_partials<T, N, R, NT>(A, blk, y0, rl);
-    for (int e = tid; e < R * N; e += NT) {
-      const int r = e / N, x = e % N;
-      const T w = rl(0, r, x), vx = rl(1, r, x), vy = rl(2, r, x);
-      T Kv;
-      if constexpr (Geo::STAGE_K) Kv = ks[e];
-      else Kv = A.K[(size_t)(y0 + r) * N + x];
-      // explicit fused multiply-adds: every kernel instantiation (single and batched) rounds
-      // the same way
-      const T v2 = fma(vx, vx, vy * vy);
-      const T c1 = fma(-A.b, v2, -(A.gv * Kv));        // velocity terms: -b|v|^2 v - gamma_v K v = c1 v
-      const T lw = A.lam * w;                           // advection, conservative form
-      rl(0, r, x) = fma(c1, vx, lw * vy);
-      rl(1, r, x) = fma(c1, vy, -(lw * vx));
-      rl(2, r, x) = -(A.gw * Kv) * w;
-    }
+    // the real-space terms in place; a recorded step also adds every point to the
+    // time-series sums as it reads it
+    auto terms = [&](auto rec_tag) {
+      constexpr bool RS = decltype(rec_tag)::value;
+      SeriesSums<T> ss;
+      const T dx = (T)A.dx, cx = (T)A.cx, cy = (T)A.cy;
+      for (int e = tid; e < R * N; e += NT) {
+        const int r = e / N, x = e % N;
+        const T w = rl(0, r, x), vx = rl(1, r, x), vy = rl(2, r, x);
+        if constexpr (RS) ss.add(w, vx, vy, (T)(x - N / 2) * dx - cx, (T)(y0 + r - N / 2) * dx - cy);
+        T Kv;
+        if constexpr (Geo::STAGE_K) Kv = ks[e];
+        else Kv = A.K[(size_t)(y0 + r) * N + x];
+        // explicit fused multiply-adds: every kernel instantiation (single and batched)
+        // rounds the same way
+        const T v2 = fma(vx, vx, vy * vy);
+        const T c1 = fma(-A.b, v2, -(A.gv * Kv));        // velocity terms: -b|v|^2 v - gamma_v K v = c1 v
+        const T lw = A.lam * w;                           // advection, conservative form
+        rl(0, r, x) = fma(c1, vx, lw * vy);
+        rl(1, r, x) = fma(c1, vy, -(lw * vx));
+        rl(2, r, x) = -(A.gw * Kv) * w;
+      }
+      if constexpr (RS) ss.template store<NT>(A, blk);
+    };
+    if (REC && A.rec != nullptr) terms(std::true_type{});
+    else terms(std::false_type{});
   } else if constexpr (KIND == ROW_FWD_VEL || KIND == ROW_FWD_MASK) {
     for (int e = tid; e < FF * R * N; e += NT) {
       const int x = e % N;
@@ -759,69 +844,70 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
         atomicMax(reinterpret_cast<unsigned long long*>(A.aux), (unsigned long long)__double_as_longlong(dmax));
         atomicMax(reinterpret_cast<unsigned long long*>(A.aux) + 1, (unsigned long long)__double_as_longlong(kvmax));
       }
-      return;
     }
 
-    // ---- update: integrating-factor Euler, k = 0, 1/2 rule ----
-    for (int j = tid; j < NK; j += NT) {
-      const int ky = ky_of(j);
-      const int m2 = kx * kx + ky * ky;
-      cplx<T> wn;
-      if constexpr (MODE == COL_STEP) {
-        const T k2 = A.dk * A.dk * (T)m2;
-        const T om = (T)1 - k2;
-        const T E = exp((A.a - om * om) * A.dt);
-        const cplx<T> w = ws[j];
-        const cplx<T> r = acc[j] * invN;
-        wn = (w + r * A.dt) * E;
-        if (m2 == 0 || m2 > M * M) wn = mk<T>(0, 0);
-      } else if constexpr (MODE == COL_PROJECT) {
-        wn = acc[j] * invN;
-        if (m2 == 0 || m2 > M * M) wn = mk<T>(0, 0);
-      } else if constexpr (MODE == COL_ADDW) {
-        // correction delta^ = DFT[delta omega] on the 1/2-rule disc, delta^(0) = 0
-        wn = acc[j] * invN;
-        if (m2 == 0 || m2 > M * M) wn = mk<T>(0, 0);
-      } else {   // COL_MASK: keep |m|^2 <= (N/8)^2, fold both 1/N factors of the round trip
-        wn = acc[j] * (invN * invN);
-        if (m2 > (N / 8) * (N / 8)) wn = mk<T>(0, 0);
-      }
-      acc[j] = wn;
-    }
-    if constexpr (MODE == COL_STEP || MODE == COL_PROJECT) {
-      if (kx == 0 && tid == 0) {
-        for (int c = 0; c < 2; ++c) {
-          T vm;
-          if constexpr (MODE == COL_STEP)
-            vm = A.mean_decay * (A.vmean[c] + A.dt * (s0[c] * invN));   // Eq. (avg)
-          else
-            vm = s0[c] * invN;                                              // DFT[v](0)
-          s0[2 + c] = vm;
-          A.vmean[c] = vm;
+    if constexpr (MODE != COL_DIV) {   // the divergence check ends with its maxima
+      // ---- update: integrating-factor Euler, k = 0, 1/2 rule ----
+      for (int j = tid; j < NK; j += NT) {
+        const int ky = ky_of(j);
+        const int m2 = kx * kx + ky * ky;
+        cplx<T> wn;
+        if constexpr (MODE == COL_STEP) {
+          const T k2 = A.dk * A.dk * (T)m2;
+          const T om = (T)1 - k2;
+          const T E = exp((A.a - om * om) * A.dt);
+          const cplx<T> w = ws[j];
+          const cplx<T> r = acc[j] * invN;
+          wn = (w + r * A.dt) * E;
+          if (m2 == 0 || m2 > M * M) wn = mk<T>(0, 0);
+        } else if constexpr (MODE == COL_PROJECT) {
+          wn = acc[j] * invN;
+          if (m2 == 0 || m2 > M * M) wn = mk<T>(0, 0);
+        } else if constexpr (MODE == COL_ADDW) {
+          // correction delta^ = DFT[delta omega] on the 1/2-rule disc, delta^(0) = 0
+          wn = acc[j] * invN;
+          if (m2 == 0 || m2 > M * M) wn = mk<T>(0, 0);
+        } else {   // COL_MASK: keep |m|^2 <= (N/8)^2, fold both 1/N factors of the round trip
+          wn = acc[j] * (invN * invN);
+          if (m2 > (N / 8) * (N / 8)) wn = mk<T>(0, 0);
         }
+        acc[j] = wn;
       }
-    }
-    block_sync<NT>();
-    if constexpr (MODE == COL_STEP || MODE == COL_PROJECT || MODE == COL_ADDW) {
-      // Hermitian average; with half-spectrum storage only mx = 0 pairs are stored
-      if (kx == 0) {
-        for (int ky = 1 + tid; ky <= M; ky += NT) {
-          const cplx<T> p = acc[ky], q = acc[NK - ky];
-          const cplx<T> h = (p + conjg(q)) * (T)0.5;
-          acc[ky] = h;
-          acc[NK - ky] = conjg(h);
-        }
-        block_sync<NT>();
-      }
-      if constexpr (MODE == COL_ADDW) {
-        for (int j = tid; j < NK; j += NT) acc[j] = acc[j] + ws[j];
+      if constexpr (MODE == COL_STEP || MODE == COL_PROJECT) {
         if (kx == 0 && tid == 0) {
-          s0[2] = A.vmean[0];
-          s0[3] = A.vmean[1];
+          for (int c = 0; c < 2; ++c) {
+            T vm;
+            if constexpr (MODE == COL_STEP)
+              vm = A.mean_decay * (A.vmean[c] + A.dt * (s0[c] * invN));   // Eq. (avg)
+            else
+              vm = s0[c] * invN;                                              // DFT[v](0)
+            s0[2 + c] = vm;
+            A.vmean[c] = vm;
+          }
         }
-        block_sync<NT>();
       }
-      for (int j = tid; j < NK; j += NT) A.what[(size_t)kx * NK + j] = acc[j];
+      block_sync<NT>();
+      if constexpr (MODE == COL_STEP || MODE == COL_PROJECT || MODE == COL_ADDW) {
+        // Hermitian average; with half-spectrum storage only mx = 0 pairs are stored
+        if (kx == 0) {
+          for (int ky = 1 + tid; ky <= M; ky += NT) {
+            const cplx<T> p = acc[ky], q = acc[NK - ky];
+            const cplx<T> h = (p + conjg(q)) * (T)0.5;
+            acc[ky] = h;
+            acc[NK - ky] = conjg(h);
+          }
+          block_sync<NT>();
+        }
+        if constexpr (MODE == COL_ADDW) {
+          for (int j = tid; j < NK; j += NT) acc[j] = acc[j] + ws[j];
+          if (kx == 0 && tid == 0) {
+            s0[2] = A.vmean[0];
+            s0[3] = A.vmean[1];
+          }
+          block_sync<NT>();
+        }
+        for (int j = tid; j < NK; j += NT) A.what[(size_t)kx * NK + j] = acc[j];
+      }
     }
   } else {
     for (int j = tid; j < NK; j += NT) acc[j] = A.what[(size_t)kx * NK + j];
@@ -833,39 +919,41 @@ __device__ __forceinline__ void col_body(const Args<T>& A, int kx, unsigned char
     block_sync<NT>();
   }
 
-  // ---- inverse column transforms of the fields the next row pass reads ----
-  constexpr int NI = Geo::NI;
-  for (int f0 = 0; f0 < NI; f0 += FB) {
-    const int nb = cmin(FB, NI - f0);
-    // spectral multipliers of the four fields, applied as the first stage's input functor
-    auto load = [&](int bt, int idx) -> cplx<T> {
-      const int f = f0 + bt;
-      const int ky = idx <= N / 2 ? idx : idx - N;
-      cplx<T> v = mk<T>(0, 0);
-      if (ky >= -M && ky <= M) {
-        const cplx<T> w = acc[ky >= 0 ? ky : ky + NK];
-        if constexpr (MODE == COL_MASK) {
-          v = w;
-        } else {
-          const T kyp = A.dk * (T)ky;
-          const int m2 = kx * kx + ky * ky;
-          const T k2 = A.dk * A.dk * (T)m2;
-          const T inv = m2 > 0 ? invN / k2 : (T)0;
-          if (f == 0) v = w * invN;                       // omega
-          else if (f == 1) v = mul_i(w) * (kyp * inv);    // v^x = i ky psi^   (stream function)
-          else v = mul_i(w) * (-kxp * inv);               // v^y = -i kx psi^
-          if (m2 == 0 && f >= 1) v = mk<T>(s0[2 + (f - 1)] * invN, (T)0);   // mean flow
+  if constexpr (MODE != COL_DIV) {
+    // ---- inverse column transforms of the fields the next row pass reads ----
+    constexpr int NI = Geo::NI;
+    for (int f0 = 0; f0 < NI; f0 += FB) {
+      const int nb = cmin(FB, NI - f0);
+      // spectral multipliers of the four fields, applied as the first stage's input functor
+      auto load = [&](int bt, int idx) -> cplx<T> {
+        const int f = f0 + bt;
+        const int ky = idx <= N / 2 ? idx : idx - N;
+        cplx<T> v = mk<T>(0, 0);
+        if (ky >= -M && ky <= M) {
+          const cplx<T> w = acc[ky >= 0 ? ky : ky + NK];
+          if constexpr (MODE == COL_MASK) {
+            v = w;
+          } else {
+            const T kyp = A.dk * (T)ky;
+            const int m2 = kx * kx + ky * ky;
+            const T k2 = A.dk * A.dk * (T)m2;
+            const T inv = m2 > 0 ? invN / k2 : (T)0;
+            if (f == 0) v = w * invN;                       // omega
+            else if (f == 1) v = mul_i(w) * (kyp * inv);    // v^x = i ky psi^   (stream function)
+            else v = mul_i(w) * (-kxp * inv);               // v^y = -i kx psi^
+            if (m2 == 0 && f >= 1) v = mk<T>(s0[2 + (f - 1)] * invN, (T)0);   // mean flow
+          }
         }
+        return v;
+      };
+      fft_batch<T, N, PE, +1, NT, N, 0>(buf, nb, tw, stab, load);
+      if (f0 + nb >= NI) griddep_launch();   // only the last stores are left (see the row pass)
+      for (int e = tid; e < nb * N; e += NT) {
+        const int b = e / N, y = e % N;
+        A.G[((size_t)(f0 + b) * H + kx) * N + y] = buf[b * LP + padi<PS>(y)];
       }
-      return v;
-    };
-    fft_batch<T, N, PE, +1, NT, N, 0>(buf, nb, tw, stab, load);
-    if (f0 + nb >= NI) griddep_launch();   // only the last stores are left (see the row pass)
-    for (int e = tid; e < nb * N; e += NT) {
-      const int b = e / N, y = e % N;
-      A.G[((size_t)(f0 + b) * H + kx) * N + y] = buf[b * LP + padi<PS>(y)];
+      block_sync<NT>();
     }
-    block_sync<NT>();
   }
 }
 
@@ -894,6 +982,7 @@ col_kernel(Args<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if constexpr (MODE == COL_STEP) {
     if (blockIdx.x == ColGeo<T, N, MODE, PEV>::H) {   // launched only for a recorded step
+      static_assert(ColGeo<T, N, MODE, PEV>::NT >= 32, "the sample block needs a whole warp 0");
       record_sample(A);
       return;
     }
@@ -906,8 +995,8 @@ template <typename T, int N, int KIND, int R, int PEV>
 __global__ void __launch_bounds__(RowGeo<T, N, KIND, R, PEV>::NT)
 row_kernel_batched(const Args<T>* __restrict__ args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const Args<T> A = args[blockIdx.y];   // tma is 0 in packed argument blocks
-  row_body<T, N, KIND, R, PEV>(A, blockIdx.x, smem_base128(smem_raw), nullptr);
+  const Args<T> A = args[blockIdx.y];   // tma is 0 and rec null in packed argument blocks
+  row_body<T, N, KIND, R, PEV, 1, 0, false>(A, blockIdx.x, smem_base128(smem_raw), nullptr);
 }
 
 template <typename T, int N, int MODE, int PEV>

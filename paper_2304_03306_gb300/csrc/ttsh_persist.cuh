@@ -119,7 +119,7 @@ __device__ __noinline__ void persist_row(const Args<T>& Ag, int blk, unsigned ch
   using S = PersistShape<T, N>;
   if (threadIdx.x < S::RG::NT) {
     const Args<T> A = Ag;
-    row_body<T, N, ROW_STEP, S::R, S::RPE>(A, blk, smem, nullptr);
+    row_body<T, N, ROW_STEP, S::R, S::RPE, 1, 0, false>(A, blk, smem, nullptr);
   }
 }
 template <typename T, int N>

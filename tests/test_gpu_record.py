@@ -41,6 +41,18 @@ def close(a, b, tol, floor=1e-3):
     return abs(a - b) <= tol * max(abs(b), floor)
 
 
+# Psi = (S2 / S3 - 2/pi) / (1 - 2/pi) is an affine map of the ratio S2 / S3 of two sums (Sec.
+# III.C), so a relative rounding error e of that ratio moves Psi by e (|Psi| + (2/pi) /
+# (1 - 2/pi)): near Psi = 0 the error is relative to the ratio, not to Psi.
+PSI_OFFSET = (2 / np.pi) / (1 - 2 / np.pi)
+
+
+def close_q(kind, a, b, tol):
+    if kind == "psi":
+        return abs(a - b) <= tol * (abs(b) + PSI_OFFSET)
+    return close(a, b, tol)
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_recorded_series_matches_oracle(T, prec):
     n, dx = 128, 0.16
@@ -56,7 +68,7 @@ def test_recorded_series_matches_oracle(T, prec):
     for j in range(5):
         o = O.diagnostics(s, p, center=CENTRE)
         for c, k in ((1, "energy"), (2, "enstrophy"), (3, "psi")):
-            assert close(ser[j, c], o[k], tol), (j, k, ser[j, c], o[k])
+            assert close_q(k, ser[j, c], o[k], tol), (j, k, ser[j, c], o[k])
         s = O.run(s, K, p, 10)
 
 
@@ -71,7 +83,7 @@ def test_record_graph_path_keeps_trajectory_and_matches_diagnostics(T, prec):
         d = b.diagnostics(centre=CENTRE)
         assert ser[j, 0] == b.steps == 10 * j
         for c, k in ((1, "energy"), (2, "enstrophy"), (3, "psi")):
-            assert close(ser[j, c], d[k], tol), (j, k, ser[j, c], d[k])
+            assert close_q(k, ser[j, c], d[k], tol), (j, k, ser[j, c], d[k])
         b.step(10)
     wa, va = a.spectral_state()
     wb, vb = b.spectral_state()
@@ -87,7 +99,7 @@ def test_record_sparse_samples_and_repeatability(T):
     for j in range(3):
         d = b.diagnostics()
         for c, k in ((1, "energy"), (2, "enstrophy"), (3, "psi")):
-            assert close(ser[j, c], d[k], 2e-6)
+            assert close_q(k, ser[j, c], d[k], 2e-6), (j, k, ser[j, c], d[k])
         b.step(min(100, 250 - b.steps))
     assert np.array_equal(a.spectral_state()[0], b.spectral_state()[0])
     # the same run again gives the same bits
