@@ -217,7 +217,7 @@ ttsh_status ttsh_time_kernels(ttsh_domain* d, int32_t iters, double* ms);
  * float row variants transform in place (no separate forward buffers), so that two blocks
  * fit per SM and one block's staging and stores overlap the other's transforms.  ttsh_set_plan
  * selects variants by index (TTSH_E_INVALID if out of range).  ttsh_autotune times each row
- * variant with its G tile staged both ways (see ttsh_set_launch_mode), keeps the fastest
+ * variant with its G tile staged both ways where it can be (see ttsh_set_launch_mode), keeps the fastest
  * (variant, staging) pair, and then times whole steps (graphs of up to 64 steps, state
  * restored) with and without programmatic dependent launch and keeps the faster. */
 ttsh_status ttsh_autotune(ttsh_domain* d, int32_t iters, int32_t* plan);
@@ -230,8 +230,10 @@ ttsh_status ttsh_set_plan(ttsh_domain* d, int32_t row_variant, int32_t col_varia
  *          (griddepcontrol.wait) before it reads anything that pass wrote;
  *   bit 1  the row pass loads its G tile with the tensor-memory accelerator (one 2D tile load
  *          per field, completion on an mbarrier with a bounded wait) instead of cp.async,
- *          where the tile allows it (N <= 512 and a row segment of R complex values a
- *          multiple of 16 bytes); elsewhere cp.async is used whatever the bit.
+ *          where the tile allows it (N <= 512, a row segment of R complex values a multiple
+ *          of 16 bytes, and a dense tile: variants whose staged tile has a spare slot per
+ *          column against shared-memory bank conflicts do not qualify); elsewhere cp.async
+ *          is used whatever the bit.
  * Results are bit-identical in every mode; values outside [0, 3] -> TTSH_E_INVALID.  The
  * paper has no counterpart: these are scheduling options. */
 ttsh_status ttsh_set_launch_mode(ttsh_domain* d, int32_t mode);

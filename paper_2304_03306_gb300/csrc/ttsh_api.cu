@@ -1262,7 +1262,7 @@ ttsh_status ttsh_autotune(ttsh_domain* d, int32_t iters, int32_t* plan) {
   double best = 1e300;
   int br = 0, bc = 0, btma = 0;
   for (int i = 0; i < d->ops.n_row_variants; ++i) {
-    for (int tma = 0; tma < 2; ++tma) {   // G tile by cp.async, then by TMA (where the tile allows)
+    for (int tma = 0; tma < 1 + d->ops.row_step[i].tma; ++tma) {   // G tile by cp.async, then by TMA (where the tile allows)
       d->dev.use_tma = tma;
       double t;
       if ((st = time_launches(d, d->ops.row_step[i].fn, iters, &t)) != TTSH_OK) return st;

@@ -137,6 +137,10 @@ __host__ __device__ constexpr int row_stride(int LP, int R, int words) {
   return R == 1 ? LP : LP + ((((32 / R) / words) % (32 / words) - LP % (32 / words)) % (32 / words) + (32 / words)) % (32 / words);
 }
 
+// Blocks of a kernel with `smem` bytes of dynamic shared memory that fit an SM's 228 KB,
+// counting the 1 KB the runtime reserves per block and up to kRecSmem of static shared memory.
+__host__ __device__ constexpr int smem_blocks_per_sm(int smem) { return (228 * 1024) / (smem + kRecSmem + 1024); }
+
 // Row-pass geometry and shared-memory plan.  CL > 1: the step kernel runs as clusters of CL
 // blocks over CL * R consecutive rows; each block stages one CL-th of the stored columns for
 // all the cluster's rows (global segments of CL * R values instead of R), and the blocks
@@ -167,20 +171,38 @@ struct RowGeo {
   // block stages HC columns (its share) of RS rows (the cluster's).
   static constexpr int HC = (H + CL - 1) / CL;
   static constexpr int RS = R * CL;
-  static constexpr int GPS = align128(HC * RS * CB);
-  static constexpr int GIN_BYTES = NPL * GPS;
+  static constexpr int GIN_DENSE = NPL * align128(HC * RS * CB);   // decides what is staged
   static constexpr int KS_BYTES = KIND == ROW_STEP ? align16(R * N * (int)sizeof(T)) : 0;
   static constexpr int RED_BYTES = KIND == ROW_INV_DIAG ? kDiagQ * 1024 * 8 : 0;
   static constexpr bool STAGE_K = KS_BYTES > 0 && CMP == 0 && TW_BYTES + BUF_BYTES + KS_BYTES + RED_BYTES <= kSmemLimit;
-  static constexpr bool STAGE_G = GIN_BYTES > 0 &&
-      TW_BYTES + BUF_BYTES + GIN_BYTES + (STAGE_K ? KS_BYTES : 0) + RED_BYTES <= kSmemLimit;
+  static constexpr bool STAGE_G = GIN_DENSE > 0 &&
+      TW_BYTES + BUF_BYTES + GIN_DENSE + (STAGE_K ? KS_BYTES : 0) + RED_BYTES <= kSmemLimit;
   // step kernel: the forward transforms get buffers of their own when they fit, so that the
   // real-space terms can be the first forward stage's input functor (read from the inverse
   // buffers, no in-place pass)
   // (float only: in double the duplicated c1 arithmetic costs more DP-pipe time than the
   // saved pass)
   static constexpr bool SEPARATE = KIND == ROW_STEP && sizeof(T) == 4 && STAGE_K && CMP == 0 &&
-      TW_BYTES + 2 * BUF_BYTES + (STAGE_G ? GIN_BYTES : 0) + KS_BYTES <= kSmemLimit;
+      TW_BYTES + 2 * BUF_BYTES + (STAGE_G ? GIN_DENSE : 0) + KS_BYTES <= kSmemLimit;
+  // Slots per mx in a staged plane.  The first inverse stage reads one row's consecutive mx
+  // across the lanes of a half-warp (8-byte values) or quarter-warp (16-byte values): with an
+  // odd number of slots per mx they meet every bank once; with an even one (R slots) two or
+  // four of them share a bank.  So without clusters (whose shares are exchanged in 16-byte
+  // pieces) an even R gets one spare slot, where the padded tile still fits the budget that
+  // decided the staging above.
+  // Nor may the padding cost a block per SM (batched launches run several per SM): the
+  // padded plan must leave as many blocks per SM as the dense one.
+  static constexpr int RS_ODD = RS % 2 == 1 ? RS : RS + 1;
+  static constexpr int PAD_EXTRA = STAGE_G ? NPL * (align128(HC * RS_ODD * CB) - align128(HC * RS * CB)) : 0;
+  static constexpr int SMEM_DENSE = align128(TW_BYTES + BUF_BYTES) + (STAGE_G ? GIN_DENSE : 0) +
+      (STAGE_K ? KS_BYTES : 0) + RED_BYTES + (SEPARATE ? BUF_BYTES : 0) + 128;
+  static constexpr bool PAD_G = CL == 1 && STAGE_G && RS_ODD != RS &&
+      TW_BYTES + (SEPARATE ? 2 : 1) * BUF_BYTES + GIN_DENSE + PAD_EXTRA + (STAGE_K ? KS_BYTES : 0) + RED_BYTES <=
+          kSmemLimit &&
+      smem_blocks_per_sm(SMEM_DENSE + PAD_EXTRA) == smem_blocks_per_sm(SMEM_DENSE);
+  static constexpr int RSP = PAD_G ? RS_ODD : RS;
+  static constexpr int GPS = align128(HC * RSP * CB);
+  static constexpr int GIN_BYTES = NPL * GPS;
   static constexpr int OFF_BUF = TW_BYTES;
   static constexpr int OFF_GIN = align128(OFF_BUF + BUF_BYTES);
   static constexpr int OFF_KS = OFF_GIN + (STAGE_G ? GIN_BYTES : 0);
@@ -188,12 +210,14 @@ struct RowGeo {
   static constexpr int OFF_FWD = OFF_RED + RED_BYTES;
   // + 128: the kernel aligns its dynamic shared-memory base to 128 bytes
   static constexpr int SMEM = OFF_FWD + (SEPARATE ? BUF_BYTES : 0) + 128;
+  static_assert(SMEM == SMEM_DENSE + (PAD_G ? PAD_EXTRA : 0), "shared-memory plan and its dense estimate disagree");
   // the G tile can come by TMA: one box of R rows x (N/4+1) columns per plane (at most 256
   // columns in a box; a row segment of R complex values a multiple of 16 bytes)
-  static constexpr bool TMA_OK = CL == 1 && STAGE_G && H <= 256 && (R * CB) % 16 == 0;
+  static constexpr bool TMA_OK = CL == 1 && STAGE_G && !PAD_G && H <= 256 && (R * CB) % 16 == 0;
   static constexpr int NT = cmax(64, cmin(1024, F * R * TT));
   static constexpr int SEG = RS * CB;                       // bytes per (plane, mx) segment
-  static constexpr int CHUNK = SEG % 16 == 0 ? 16 : 8;
+  static constexpr int SEGP = RSP * CB;                     // bytes between consecutive segments
+  static constexpr int CHUNK = SEG % 16 == 0 && SEGP % 16 == 0 ? 16 : 8;
   static constexpr bool VALID = SMEM + (KIND == ROW_STEP ? kRecSmem : 0) <= 227 * 1024 && N % R == 0 &&
                                 R <= N && TT <= 1024 && NT % TT == 0 &&
                                 (CL == 1 || (CL == 2 && KIND == ROW_STEP && STAGE_G && (N / R) % CL == 0 &&
@@ -510,7 +534,8 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
         const char* gsrc = reinterpret_cast<const char*>(A.G + ((size_t)pl * H + cbase) * N + yc);
         char* gdst = reinterpret_cast<char*>(gin) + pl * Geo::GPS;
         for (int i = tid; i < ccnt * CPS; i += NT)   // i = j * CPS + c: the plane is [mx][r]
-          cp_async<Geo::CHUNK>(gdst + i * Geo::CHUNK, gsrc + (size_t)(i / CPS) * N * Geo::CB + (i % CPS) * Geo::CHUNK);
+          cp_async<Geo::CHUNK>(gdst + (i / CPS) * Geo::SEGP + (i % CPS) * Geo::CHUNK,
+                               gsrc + (size_t)(i / CPS) * N * Geo::CB + (i % CPS) * Geo::CHUNK);
       }
     }
   }
@@ -531,8 +556,8 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
       if constexpr (Geo::STAGE_G) {
         if constexpr (CL == 1) {
           const cplx<T>* src = gin + (size_t)f * GPC + r;
-          if (k <= M) X = src[k * R];
-          if (km <= M) Xm = src[km * R];
+          if (k <= M) X = src[k * Geo::RSP];
+          if (km <= M) Xm = src[km * Geo::RSP];
         } else {
           // column kk of this block's row r: slot (kk - o HC, c R + r) of the share of block
           // o that owns it, read through distributed shared memory when o is the other block

@@ -60,6 +60,7 @@ struct StepVariant {
   int pe;
   int cl;    // blocks per cluster (row pass)
   int cmp;   // 1: compact row pass (in-place forward transforms)
+  int tma;   // 1: the row pass can stage its G tile by TMA (launch mode bit 1)
 };
 
 constexpr int kMaxBatchN = 1024;

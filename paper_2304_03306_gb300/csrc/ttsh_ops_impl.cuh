@@ -194,7 +194,8 @@ static void add_row_variant(SizeOps& o) {
       if (o.row_step[i].rows == R && o.row_step[i].pe == cmin(PE, N / 2) && o.row_step[i].cl == CL &&
           o.row_step[i].cmp == cmp)
         return;   // same shape
-    StepVariant v{&launch_row_kind<T, N, ROW_STEP, R, PE, CL, CMP>, nullptr, nullptr, R, cmin(PE, N / 2), CL, cmp};
+    StepVariant v{&launch_row_kind<T, N, ROW_STEP, R, PE, CL, CMP>, nullptr, nullptr, R, cmin(PE, N / 2), CL, cmp,
+                  RowGeo<T, N, ROW_STEP, R, PE, CL, CMP>::TMA_OK ? 1 : 0};
     if constexpr (N <= kMaxBatchN && CL == 1 && CMP == 0) {
       v.batched = &launch_row_batched<T, N, R, PE>;
       v.prepare = &prepare_row_batched<T, N, R, PE>;
