@@ -179,8 +179,9 @@ ttsh_status ttsh_diagnostics(ttsh_domain* d, ttsh_diag* out, double* spectrum, i
  * ceil(nsteps / every) samples) is sampled inside that step's row pass, which already holds
  * omega, v_x and v_y in real space.  Sample j is written to series[5 j .. 5 j + 4] =
  * {step count, energy, enstrophy, psi, number of non-finite points}, with the definitions of
- * ttsh_diag; per-thread and per-warp partial sums are taken in the domain precision and
- * the warps' sums combined in double, all in a fixed order (repeatable bits).  To record the state after the last step, call
+ * ttsh_diag; per-thread, per-warp and per-block partial sums are taken in the domain
+ * precision and the blocks' sums combined as double-float pairs (float domains) or in double,
+ * all in a fixed order (repeatable bits).  To record the state after the last step, call
  * ttsh_diagnostics afterwards.
  *   every     >= 1 steps between samples.
  *   series    device (or managed) memory of at least 5 * capacity doubles, owned by the
