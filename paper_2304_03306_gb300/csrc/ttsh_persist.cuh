@@ -51,6 +51,16 @@ struct PDomain {
   int pad;
 };
 
+// An item as the body threads read it: its list entry, its domain's grid size and argument
+// block, copied into shared memory by the control lane while the previous item runs (so the
+// body starts without a global-memory round trip).
+template <typename T>
+struct PStaged {
+  Args<T> A;
+  PItem it;
+  int n;
+};
+
 // Control block, zeroed before every launch: [0] next item, [1] abort flag, then per domain
 // [2 + 2d] row items done, [3 + 2d] column items done.
 constexpr int kPersistCtlHead = 0, kPersistCtlAbort = 1, kPersistCtlDone = 2;
@@ -166,6 +176,7 @@ persistent_step_kernel(const PDomain<T>* __restrict__ doms, const PItem* __restr
   unsigned char* smem = smem_base128(smem_raw);
   __shared__ long long s_item[2];
   __shared__ int s_fast[2];
+  __shared__ PStaged<T> s_st[2];
   __shared__ volatile long long s_body_done;   // the last item whose body thread 0 finished
   const long long total = nsteps * (long long)ips;
   const bool ctrl = threadIdx.x == NB;
@@ -186,10 +197,18 @@ persistent_step_kernel(const PDomain<T>* __restrict__ doms, const PItem* __restr
     const long long g = (long long)atomicAdd(&ctl[kPersistCtlHead], 1ull);
     return (g >= total || ld_relaxed_u64(abort_flag)) ? -1 : g;
   };
+  // control lane: copy item g's record, size and arguments into staging slot sl
+  auto stage = [&](long long g, int sl) {
+    const PItem it = items[g % ips];
+    s_st[sl].it = it;
+    s_st[sl].n = doms[it.dom].n;
+    s_st[sl].A = doms[it.dom].A;
+  };
 
   unsigned long long* pending = nullptr;   // control lane: the completion signal still to send
   if (ctrl) {
     long long g = take();
+    if (g >= 0) stage(g, 0);
     if (g >= 0 && !wait_ready(items[g % ips], g)) g = -1;
     fence_proxy_async_global();   // the column pass reads Rr with bulk copies
     s_item[0] = g;
@@ -202,12 +221,12 @@ persistent_step_kernel(const PDomain<T>* __restrict__ doms, const PItem* __restr
       if (pending) red_release_add_u64(pending, 1ull);
       return;
     }
-    const PItem it = items[g % ips];
+    const PItem it = s_st[slot].it;
     long long gn = -1;
     bool ready = false;
     if (threadIdx.x < NB) {
-      const Args<T>& A = doms[it.dom].A;   // read in place (the table is not written during the launch)
-      switch (doms[it.dom].n) {
+      const Args<T>& A = s_st[slot].A;
+      switch (s_st[slot].n) {
         case 16: persist_item<T, 16>(A, it.phase, it.blk, smem); break;
         case 32: persist_item<T, 32>(A, it.phase, it.blk, smem); break;
         case 64: persist_item<T, 64>(A, it.phase, it.blk, smem); break;
@@ -224,6 +243,7 @@ persistent_step_kernel(const PDomain<T>* __restrict__ doms, const PItem* __restr
       }
       gn = take();
       if (gn >= 0) {
+        stage(gn, slot ^ 1);   // slot ^ 1 was read by the previous item, which is done
         unsigned long long* ctr;
         unsigned long long need;
         item_need(doms, items[gn % ips], gn / ips, ctl, &ctr, &need);
