@@ -256,6 +256,16 @@ __device__ __forceinline__ void stage_sync() {
 // Marker: the first stage reads its inputs from the buffer (no input functor).
 struct NoLoad {};
 
+// Index of element i in the buffer one stage hands the next where a padded layout puts
+// several lanes of a wavefront on one bank (see stockham_stage): every aligned group of 16
+// slots rotated, by 4 ((i >> 4) mod 4) for transforms with 4 points per thread and by
+// 8 ((i >> 6) mod 2) for 8 points per thread - a bijection of the unpadded indices.
+template <int PE>
+__device__ __forceinline__ int handoff_slot(int i) {
+  if constexpr (PE == 4) return (i & ~15) | ((i + ((i >> 2) & 12)) & 15);
+  else return (i & ~15) | ((i + ((i >> 3) & 8)) & 15);
+}
+
 // One Stockham stage of radix R on a length-L transform at buf (padded), current
 // sub-transform length Ns.  j: this thread's index among the L/PE owners.  In the first
 // stage (Ns = 1) an input functor ld(bi, m) may supply element m of transform bi instead of
@@ -275,6 +285,15 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
   constexpr int SL = L / R;   // stride of a butterfly's inputs
   constexpr bool LD_OFF = SL % (1 << PS) == 0 || L <= (1 << PS);
   constexpr bool ST_OFF = Ns % (1 << PS) == 0 || Ns * R <= (1 << PS);
+  // With PE = 4 or 8 points per thread the stage at Ns = PE stores (q - k) PE + k + PE r: in
+  // the padded layout the lanes of a wavefront with equal k and consecutive q / PE share a
+  // bank (four or two wavefronts where one would do).  Its output, read only by the stage at
+  // Ns = PE^2, is stored by handoff_slot<PE> instead, under which those stores and that stage's
+  // loads (consecutive indices) meet every bank once: for 8- and 16-byte elements at PE = 4,
+  // for 8-byte ones at PE = 8 (16-byte ones meet no conflict there).
+  constexpr bool ROTATE = PE == 4 || (PE == 8 && sizeof(T) == 4);
+  constexpr bool ROT_OUT = ROTATE && Ns == PE && R == PE && Ns * R < L;
+  constexpr bool ROT_IN = ROTATE && Ns == PE * PE && L > PE * PE;
   cplx<T> v[NB][R];
   if (active) {
 #pragma unroll
@@ -283,6 +302,9 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
       if constexpr (FUSED) {
 #pragma unroll
         for (int r = 0; r < R; ++r) v[b][r] = ld(bi, q + r * SL);
+      } else if constexpr (ROT_IN) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b][r] = buf[handoff_slot<PE>(q + r * SL)];
       } else if constexpr (LD_OFF) {
         const cplx<T>* p0 = buf + padi<PS>(q);
 #pragma unroll
@@ -316,7 +338,10 @@ __device__ __forceinline__ void stockham_stage(cplx<T>* buf, int j, bool active,
       }
       dft_reg<T, R, DIR>(v[b]);
       const int base = (q - k) * R + k;
-      if constexpr (ST_OFF) {
+      if constexpr (ROT_OUT) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[handoff_slot<PE>(base + r * Ns)] = v[b][bitrev<R>(r)];
+      } else if constexpr (ST_OFF) {
         cplx<T>* p0 = buf + padi<PS>(base);
 #pragma unroll
         for (int r = 0; r < R; ++r) p0[r * Ns + ((r * Ns) >> PS)] = v[b][bitrev<R>(r)];

@@ -41,6 +41,10 @@ static constexpr int kSpreadSmemBytes = 116 * 1024;
 
 // padded index: one spare slot after every 2^ps slots
 static constexpr int padded(int i, int ps) { return i + (i >> ps); }
+// the rotated layout of one stage handoff with 4 or 8 points per thread (see stockham_stage)
+static constexpr int rotated(int i, int pe) {
+  return pe == 4 ? (i & ~15) | ((i + ((i >> 2) & 12)) & 15) : (i & ~15) | ((i + ((i >> 3) & 8)) & 15);
+}
 
 template <typename T>
 static const char* tname() { return sizeof(T) == 4 ? "f32" : "f64"; }
@@ -54,12 +58,18 @@ static void check_fft(const char* who) {
   constexpr bool kStageTab = StageTab<T, L, PE>::USE;
   constexpr int kStageEntries = StageTab<T, L, PE>::ENTRIES;
   static_assert(L % PE == 0, "points per thread must divide the length");
+  // slot in which the previous stage stored each element (the input layout is padded)
+  std::vector<int> handed(L);
+  for (int i = 0; i < L; ++i) handed[i] = padded(i, PS);
   for (int Ns = 1; Ns < L;) {
     const int R = (L / Ns < PE) ? (L / Ns) : PE;
     const int SL = L / R, NB = PE / R;
     const bool ld_off = SL % (1 << PS) == 0 || L <= (1 << PS);
     const bool st_off = Ns % (1 << PS) == 0 || Ns * R <= (1 << PS);
-    std::vector<int> rd(L, 0), wr(L, 0);
+    const bool rotate = PE == 4 || (PE == 8 && sizeof(T) == 4);
+    const bool rot_out = rotate && Ns == PE && R == PE && Ns * R < L;
+    const bool rot_in = rotate && Ns == PE * PE && L > PE * PE;
+    std::vector<int> rd(L, 0), wr(L, 0), rslot(LP, 0), wslot(LP, 0), next(L, -1);
     for (int j = 0; j < TT; ++j)
       for (int b = 0; b < NB; ++b) {
         const int q = j + b * TT;
@@ -71,10 +81,17 @@ static void check_fft(const char* who) {
           if (li < 0 || li >= L || si < 0 || si >= L) continue;
           ++rd[li];
           ++wr[si];
-          CHECK(padded(li, PS) < LP && padded(si, PS) < LP, "%s L=%d Ns=%d", who, L, Ns);
-          if (ld_off)
+          const int lslot = rot_in ? rotated(li, PE) : padded(li, PS);
+          const int sslot = rot_out ? rotated(si, PE) : padded(si, PS);
+          CHECK(lslot >= 0 && lslot < LP && sslot >= 0 && sslot < LP, "%s L=%d Ns=%d", who, L, Ns);
+          if (lslot < 0 || lslot >= LP || sslot < 0 || sslot >= LP) continue;
+          ++rslot[lslot];
+          ++wslot[sslot];
+          CHECK(lslot == handed[li], "%s L=%d Ns=%d: element %d loaded from another slot than stored", who, L, Ns, li);
+          next[si] = sslot;
+          if (ld_off && !rot_in)
             CHECK(padded(li, PS) == padded(q, PS) + r * SL + ((r * SL) >> PS), "%s L=%d Ns=%d q=%d r=%d", who, L, Ns, q, r);
-          if (st_off)
+          if (st_off && !rot_out)
             CHECK(padded(si, PS) == padded(base, PS) + r * Ns + ((r * Ns) >> PS), "%s L=%d Ns=%d q=%d r=%d", who, L, Ns,
                   q, r);
           if (kStageTab && Ns > 1 && r > 0)
@@ -82,8 +99,14 @@ static void check_fft(const char* who) {
         }
       }
     for (int i = 0; i < L; ++i) CHECK(rd[i] == 1 && wr[i] == 1, "%s L=%d PE=%d Ns=%d i=%d", who, L, PE, Ns, i);
+    for (int i = 0; i < LP; ++i) CHECK(rslot[i] <= 1 && wslot[i] <= 1, "%s L=%d PE=%d Ns=%d slot=%d", who, L, PE, Ns, i);
+    // the layout a stage stores is the one the next stage loads
+    if (rot_out) CHECK(Ns * R == PE * PE, "%s L=%d: rotated output not read by the Ns = PE^2 stage", who, L);
+    handed = next;
     Ns *= R;
   }
+  // callers read the result in the padded layout
+  for (int i = 0; i < L; ++i) CHECK(handed[i] == padded(i, PS), "%s L=%d: output %d not in the padded layout", who, L, i);
 }
 
 // ------------------------------------------------------------------ row pass
