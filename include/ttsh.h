@@ -249,6 +249,8 @@ ttsh_status ttsh_set_launch_mode(ttsh_domain* d, int32_t mode);
  *   w_hat  omega^ in the half-spectrum layout above, H*NK complex (re, im interleaved),
  *          advanced in place;
  *   v0     v^(0), 2 values, advanced in place.
+ * All three must be 16-byte aligned (as cudaMalloc's are); otherwise -> TTSH_E_INVALID,
+ * before any device work.
  * Scratch (inter-pass buffers, twiddle tables) lives in one fixed device array inside the
  * library, sized for n <= 512 (about 6.4 MB, held by every GPU that loads the library until
  * the process exits); n > 512 -> TTSH_E_INVALID, as are the parameter checks of

@@ -600,7 +600,9 @@ __device__ __forceinline__ void row_body(const Args<T>& A, int blk, unsigned cha
     auto rhs = [&](int bt, int k) -> cplx<T> {
       const int f = bt / R, r = bt % R;
       const cplx<T> wz = sm[(0 * R + r) * LP + padi<PS>(k)];
-      const T k0 = ks[r * N + 2 * k], k1 = ks[r * N + 2 * k + 1];
+      // the slot's two mask values in one load (the staged rows start 16-byte aligned, N is even)
+      const cplx<T> kk = reinterpret_cast<const cplx<T>*>(ks + r * N)[k];
+      const T k0 = kk.x, k1 = kk.y;
       if (f == 2) return mk<T>(-(A.gw * k0) * wz.x, -(A.gw * k1) * wz.y);
       const cplx<T> vxz = sm[(1 * R + r) * LP + padi<PS>(k)];
       const cplx<T> vyz = sm[(2 * R + r) * LP + padi<PS>(k)];

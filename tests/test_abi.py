@@ -74,6 +74,19 @@ def test_null_arguments_are_rejected(lib):
     lib.ttsh_destroy_domain(None)   # no-op
 
 
+def test_no_allocation_step_rejects_misaligned_buffers_before_any_device_work(lib):
+    """The kernels stage the caller's mask and state with 16-byte copies: a misaligned
+    buffer is an argument error on the host (the pointers below are never dereferenced)."""
+    from paper_2304_03306_gb300 import ttsh
+    p = ttsh.ttsh_default_params(n=64, dx=0.25, precision=32)
+    good, off8 = 0x10000, 0x20008
+    for K, w, v in ((off8, good, good + 0x1000), (good, off8, good + 0x1000), (good, good + 0x1000, off8 + 0x100)):
+        st = lib.ttsh_step_noalloc(ctypes.byref(p), ctypes.c_void_p(K), ctypes.c_void_p(w), ctypes.c_void_p(v),
+                                   ctypes.c_int64(1), None)
+        assert st == ttsh.TTSH_E_INVALID
+        assert "16-byte aligned" in ttsh.ttsh_last_error()
+
+
 def test_product_path_has_no_oracle_import():
     pkg = os.path.join(ROOT, "paper_2304_03306_gb300")
     for dirpath, _, files in os.walk(pkg):
