@@ -29,8 +29,10 @@
 
 namespace ttsh {
 
+// Aligned to its size, so that a complex value moves as one 8- or 16-byte access (every
+// buffer holding them - shared-memory regions, the workspace - is 16-byte aligned).
 template <typename T>
-struct cplx {
+struct alignas(2 * sizeof(T)) cplx {
   T x, y;
 };
 

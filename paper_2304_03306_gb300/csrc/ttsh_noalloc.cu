@@ -106,9 +106,6 @@ ttsh_status setup_device(int dev, char** out) {
 extern "C" ttsh_status ttsh_step_noalloc(const ttsh_params* p, const void* K, void* w_hat, void* v0,
                                          int64_t nsteps, void* stream) {
   if (!p || !K || !w_hat || !v0) return bad(TTSH_E_INVALID, "NULL argument");
-  // the kernels stage K and w_hat with 16-byte copies and read complex values as pairs
-  if ((reinterpret_cast<uintptr_t>(K) | reinterpret_cast<uintptr_t>(w_hat) | reinterpret_cast<uintptr_t>(v0)) % 16 != 0)
-    return bad(TTSH_E_INVALID, "K, w_hat and v0 must be 16-byte aligned");
   if (p->n < 16 || (p->n & (p->n - 1)) != 0)
     return bad(TTSH_E_INVALID, "n must be a power of two >= 16");
   if (p->n > kNoAllocMaxN)
@@ -120,6 +117,9 @@ extern "C" ttsh_status ttsh_step_noalloc(const ttsh_params* p, const void* K, vo
   for (double v : c)
     if (!std::isfinite(v)) return bad(TTSH_E_INVALID, "model coefficients must be finite");
   if (nsteps < 0) return bad(TTSH_E_INVALID, "nsteps must be >= 0");
+  // the kernels stage K and w_hat with 16-byte copies and read complex values as pairs
+  if ((reinterpret_cast<uintptr_t>(K) | reinterpret_cast<uintptr_t>(w_hat) | reinterpret_cast<uintptr_t>(v0)) % 16 != 0)
+    return bad(TTSH_E_INVALID, "K, w_hat and v0 must be 16-byte aligned");
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
