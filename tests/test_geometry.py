@@ -41,3 +41,25 @@ def test_every_registered_tile_plan_stays_in_bounds():
         last = r.stdout.strip().splitlines()[-1]
         checked = int(last.split()[0])
         assert checked > 300 and last.endswith(" 0 failures"), last
+
+
+def test_checker_covers_the_registered_variants():
+    """The checker's variant lists are the registry's (csrc/ttsh_ops_impl.cuh), entry for
+    entry, so a variant added to the library cannot escape the index checks."""
+    import re
+    impl = open(os.path.join(ROOT, "paper_2304_03306_gb300", "csrc", "ttsh_ops_impl.cuh")).read()
+    chk = open(os.path.join(ROOT, "tests", "geometry_check.cu")).read()
+
+    def shapes(pattern, text):
+        return [s for s in re.findall(pattern, text) if not s.startswith("default")]
+
+    rows = shapes(r"add_row_variant<T, N, ([^>]*?)>\(o\)", impl)
+    cols = shapes(r"add_col_variant<T, N, ([^>]*?)>\(o\)", impl)
+    assert rows and cols
+    assert rows == shapes(r"check_row<T, N, ROW_STEP, ([^>]*?)>\(\)", chk)
+    assert cols == shapes(r"check_col<T, N, COL_STEP, ([^>]*?)>\(\)", chk)
+    # and both start from each size's default shapes
+    assert "add_row_variant<T, N, default_step_rows<T, N>(), default_step_row_pe<T, N>(), default_row_cluster<T, N>()>(o)" in impl
+    assert "check_row<T, N, ROW_STEP, default_step_rows<T, N>(), default_step_row_pe<T, N>(), default_row_cluster<T, N>()>()" in chk
+    assert "add_col_variant<T, N, default_step_col_pe<T, N>()>(o)" in impl
+    assert "check_col<T, N, COL_STEP, default_step_col_pe<T, N>()>()" in chk
